@@ -1,0 +1,265 @@
+"""Spatial grid, boundary fill, reconstruction and flux divergences.
+
+Follows Sec. 2.2 (Eq. radiation_integral: finite-volume / finite-solid-angle
+form), Sec. 2.3 (reconstruction of the primitive I per angle bin, in each
+dimension separately), Sec. 2.4 (Eq. flux_space, Eq. flux_angle: upwind
+fluxes) and Sec. 2.6 (angular fluxes summed over the edges of a geodesic
+cell).
+
+Layout: intensities are I[k, j, i, n] (x3, x2, x1, angle), float64.
+The boundary fill builds an extended array with two ghost cells per side in
+every flux dimension (Sec. 2 task list, "apply boundary conditions").
+"""
+import math
+
+import torch
+
+from . import DTYPE
+from . import geometry as G
+
+NG = 2
+
+
+class Grid:
+    """Logically rectangular block of cells.
+
+    kind, a   spacetime (see geometry.KINDS) and spin
+    xf        three 1-D float64 tensors of face coordinates (n_d + 1 each)
+    bc        ((lo, hi) for x1, x2, x3), each 'periodic' | 'outflow' | 'polar'
+    ndim      number of dimensions that carry fluxes (the others have one cell)
+    """
+
+    def __init__(self, kind, a, xf, bc, ndim):
+        self.kind, self.a = kind, float(a)
+        self.xf = [torch.as_tensor(x, dtype=DTYPE) for x in xf]
+        self.n = [len(x) - 1 for x in self.xf]
+        self.bc = bc
+        self.ndim = ndim
+        for d in range(ndim, 3):
+            assert self.n[d] == 1
+        self.xc = [0.5 * (x[1:] + x[:-1]) for x in self.xf]
+
+    @property
+    def shape(self):
+        return (self.n[2], self.n[1], self.n[0])
+
+    def centres(self):
+        X3, X2, X1 = torch.meshgrid(self.xc[2], self.xc[1], self.xc[0], indexing="ij")
+        return torch.stack([X1, X2, X3], dim=-1)
+
+    def polar_faces(self, d):
+        """Boolean per face index along d: faces on a polar boundary."""
+        m = torch.zeros(self.n[d] + 1, dtype=torch.bool)
+        if self.bc[d][0] == "polar":
+            m[0] = True
+        if self.bc[d][1] == "polar":
+            m[-1] = True
+        return m
+
+
+class Setup:
+    """Per-cell and per-face geometric factors of Secs. 2.1-2.2 on a grid.
+
+    All factors are evaluated at cell / face centres (coordinate midpoints):
+      e, g, omega       tetrad, metric, Ricci rotation coefficients
+      nup[..., n, mu]   n^mu = e^mu_A n^A, with n^0hat = 1
+      nlow[..., n, mu]  n_mu
+      f[..., n]         n^0 n_0  (conserved U = f I, Eq. radiation_integral)
+      dV                cell volume (exact)
+      fcoef[d]          Delta A_d n^d n_0 at every face along d
+      fsign[d]          n^d at every face along d (upwind direction)
+    """
+
+    def __init__(self, grid, ang):
+        self.grid, self.ang = grid, ang
+        kind, a = grid.kind, grid.a
+        X = grid.centres().reshape(-1, 3)
+        e = G.batched(G.tetrad, kind, a, X)
+        g = G.batched(G.metric, kind, a, X)
+        om = G.batched(G.ricci_rotation, kind, a, X)
+        sh = grid.shape
+        self.e = e.reshape(sh + (4, 4))
+        self.g = g.reshape(sh + (4, 4))
+        self.omega = om.reshape(sh + (4, 4, 4))
+        nhat = torch.cat([torch.ones(ang.n_ang, 1, dtype=DTYPE), ang.dir], dim=1)
+        self.nhat4 = nhat
+        self.nup = torch.einsum("...mA,nA->...nm", self.e, nhat)
+        self.nlow = torch.einsum("...mv,...nv->...nm", self.g, self.nup)
+        self.f = self.nup[..., 0] * self.nlow[..., 0]
+        # exact cell volumes
+        lo = torch.stack(torch.meshgrid(grid.xf[2][:-1], grid.xf[1][:-1], grid.xf[0][:-1],
+                                        indexing="ij")[::-1], dim=-1)
+        hi = torch.stack(torch.meshgrid(grid.xf[2][1:], grid.xf[1][1:], grid.xf[0][1:],
+                                        indexing="ij")[::-1], dim=-1)
+        self.dV = G.cell_volume(kind, a, lo, hi)
+        # face factors
+        self.fcoef, self.fsign = [], []
+        for d in range(grid.ndim):
+            coords = [grid.xc[0], grid.xc[1], grid.xc[2]]
+            coords[d] = grid.xf[d]
+            X3, X2, X1 = torch.meshgrid(coords[2], coords[1], coords[0], indexing="ij")
+            Xf = torch.stack([X1, X2, X3], dim=-1)
+            polar = grid.polar_faces(d)
+            # faces on the polar axis have zero area; evaluate their tetrad at
+            # a regular point (the result is multiplied by zero)
+            if polar.any():
+                idx = [slice(None)] * 3
+                idx[2 - d] = polar
+                Xf = Xf.clone()
+                Xf[tuple(idx) + (d,)] = grid.xc[d][0]
+            fsh = Xf.shape[:-1]
+            ef = G.batched(G.tetrad, kind, a, Xf.reshape(-1, 3)).reshape(fsh + (4, 4))
+            gf = G.batched(G.metric, kind, a, Xf.reshape(-1, 3)).reshape(fsh + (4, 4))
+            nupf = torch.einsum("...mA,nA->...nm", ef, nhat)
+            n0low = torch.einsum("...v,...nv->...n", gf[..., 0, :], nupf)
+            # face extents in the other two coordinates
+            flo, fhi = [], []
+            for dd in range(3):
+                if dd == d:
+                    flo.append(grid.xf[dd]); fhi.append(grid.xf[dd])
+                else:
+                    flo.append(grid.xf[dd][:-1]); fhi.append(grid.xf[dd][1:])
+            lo = torch.stack(torch.meshgrid(flo[2], flo[1], flo[0], indexing="ij")[::-1], dim=-1)
+            hi = torch.stack(torch.meshgrid(fhi[2], fhi[1], fhi[0], indexing="ij")[::-1], dim=-1)
+            dA = G.face_area(kind, a, d, lo, hi)
+            idx = [slice(None)] * 3
+            idx[2 - d] = polar
+            dA[tuple(idx)] = 0.0
+            na = nupf[..., d + 1]
+            self.fcoef.append(dA[..., None] * na * n0low)
+            self.fsign.append(na)
+
+
+# ------------------------------------------------------------ boundaries
+def fill_ghosts(I, grid, perm):
+    """Extended array with NG ghost cells per side in every flux dimension.
+
+    periodic  ghost takes the cell one period away
+    outflow   ghost copies the nearest active cell (same angle bin)
+    polar     (x2 = theta only) ghost at theta -> -theta, phi -> phi + pi takes
+              the active cell across the pole, with angle bin n taking bin
+              perm[n] (rotation by pi about the 2-axis of the spherical
+              tetrad, under which the geodesic grid is invariant)
+    """
+    N1, N2, N3 = grid.n
+    Na = I.shape[-1]
+    Ie = torch.zeros((N3 + 2 * NG, N2 + 2 * NG, N1 + 2 * NG, Na), dtype=I.dtype)
+    act = (slice(NG, NG + N3), slice(NG, NG + N2), slice(NG, NG + N1))
+    Ie[act] = I
+    for d in range(grid.ndim):
+        ax = 2 - d                       # array dimension of coordinate d
+        N = grid.n[d]
+        for side in (0, 1):
+            kind = grid.bc[d][side]
+            for gidx in range(NG):       # ghost layer 0 is adjacent to the boundary
+                if side == 0:
+                    gpos = NG - 1 - gidx
+                else:
+                    gpos = NG + N + gidx
+                if kind == "periodic":
+                    src = (N - 1 - gidx) if side == 0 else gidx
+                    shift, pm = 0, None
+                elif kind == "outflow":
+                    src = 0 if side == 0 else N - 1
+                    shift, pm = 0, None
+                elif kind == "polar":
+                    assert d == 1
+                    src = gidx if side == 0 else N - 1 - gidx
+                    shift, pm = N3 // 2, perm
+                else:
+                    raise ValueError(kind)
+                sl_dst = list(act)
+                sl_dst[ax] = slice(gpos, gpos + 1)
+                sl_src = list(act)
+                sl_src[ax] = slice(NG + src, NG + src + 1)
+                vals = Ie[tuple(sl_src)].clone()
+                if shift:
+                    vals = torch.roll(vals, shifts=-shift, dims=0)
+                if pm is not None:
+                    vals = vals[..., pm]
+                Ie[tuple(sl_dst)] = vals
+    return Ie
+
+
+# ------------------------------------------------------- reconstruction
+def van_leer(dl, dr):
+    """Harmonic-mean slope of van Leer (1974): 2 dl dr / (dl + dr) if dl dr > 0."""
+    prod = dl * dr
+    pos = prod > 0.0
+    den = torch.where(pos, dl + dr, torch.ones_like(dl))
+    return torch.where(pos, 2.0 * prod / den, torch.zeros_like(dl))
+
+
+def face_states(Ie, grid, d, recon):
+    """Left/right states of I at the n_d + 1 faces along coordinate d (Sec. 2.3)."""
+    ax = 2 - d
+    N = grid.n[d]
+    sl = [slice(NG, NG + grid.n[2]), slice(NG, NG + grid.n[1]), slice(NG, NG + grid.n[0])]
+    sl[ax] = slice(None)
+    line = Ie[tuple(sl)]                    # all NG + N + NG cells along ax
+
+    def take(lo, hi):
+        s = [slice(None)] * 4
+        s[ax] = slice(lo, hi)
+        return line[tuple(s)]
+
+    # face f (0..N) sits between extended cells f + NG - 1 and f + NG
+    IL = take(NG - 1, NG + N)
+    IR = take(NG, NG + N + 1)
+    if recon == "dc":
+        return IL, IR
+    dL = take(1, NG + N + 1) - take(0, NG + N)          # I_c - I_{c-1}, c = 1..N+NG
+    dR = take(2, NG + N + 2) - take(1, NG + N + 1)      # I_{c+1} - I_c
+    slope = van_leer(dL, dR)                            # at extended cells 1..N+NG
+    s = [slice(None)] * 4
+    s[ax] = slice(NG - 2, NG - 2 + N + 1)
+    sL = slope[tuple(s)]                                # cells NG-1 .. NG+N-1
+    s[ax] = slice(NG - 1, NG - 1 + N + 1)
+    sR = slope[tuple(s)]                                # cells NG .. NG+N
+    return IL + 0.5 * sL, IR - 0.5 * sR
+
+
+def spatial_divergence(Ie, setup, recon):
+    """(1/dV) sum_d [dA n^d n_0 I_upwind]^+_- (Eq. flux_space, Eq. radiation_integral)."""
+    grid = setup.grid
+    div = torch.zeros(grid.shape + (Ie.shape[-1],), dtype=Ie.dtype)
+    for d in range(grid.ndim):
+        ax = 2 - d
+        IL, IR = face_states(Ie, grid, d, recon)
+        up = torch.where(setup.fsign[d] < 0.0, IR, IL)     # tie -> left state
+        F = setup.fcoef[d] * up
+        N = grid.n[d]
+        hi = F.narrow(ax, 1, N)
+        lo = F.narrow(ax, 0, N)
+        div = div + (hi - lo)
+    return div / setup.dV[..., None]
+
+
+def angular_speeds(setup):
+    """Per cell and edge: l_e * (V . nu_e) * n_0(n_e)  (Eq. flux_angle, Sec. 2.6).
+
+    V is the angular velocity field on the unit sphere implied by the
+    symbols n^zeta, n^psi (the tangent part of -omega^i_{AB} n^A n^B); it is
+    evaluated at the edge midpoint n_e and projected on the edge normal nu_e
+    (from cell p to cell q).  n_0 uses the cell-centre tetrad at direction n_e.
+    """
+    ang = setup.ang
+    ne4 = torch.cat([torch.ones(len(ang.edge_len), 1, dtype=DTYPE), ang.edge_mid], dim=1)
+    Q = torch.einsum("...CAB,eA,eB->...eC", setup.omega, ne4, ne4)
+    V = -(Q[..., 1:] - ang.edge_mid * Q[..., :1])
+    s = (V * ang.edge_nrm).sum(-1)
+    n0 = torch.einsum("...v,...vA,eA->...e", setup.g[..., 0, :], setup.e, ne4)
+    return ang.edge_len * s * n0, s
+
+
+def angular_divergence(I, setup):
+    """(1/dOmega_p) sum over the edges of p of the outgoing DC-upwind flux."""
+    ang = setup.ang
+    coef, s = angular_speeds(setup)
+    p, q = ang.edges[:, 0], ang.edges[:, 1]
+    Ip, Iq = I[..., p], I[..., q]
+    F = coef * torch.where(s < 0.0, Iq, Ip)            # tie -> p side
+    div = torch.zeros_like(I)
+    div = div.index_add(-1, p, F / ang.dOmega[p])
+    div = div.index_add(-1, q, -F / ang.dOmega[q])
+    return div

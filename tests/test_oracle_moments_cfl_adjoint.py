@@ -1,0 +1,118 @@
+"""Pins of the oracle's moments (Sec. 2.5, the definition of R), its
+time-step bound, and its reverse-mode gradient (checked against central
+finite differences and by a dot-product test)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import adjoint as A
+from oracle import cfl as CF
+from oracle import moments as M
+from oracle import step as S
+from oracle.angles import GeodesicGrid
+from oracle.transport import Grid, Setup
+
+F64 = torch.float64
+
+
+def test_isotropic_moments_are_diagonal():
+    for N in (1, 2, 4):
+        ang = GeodesicGrid(N)
+        I = torch.full((2, 3, ang.n_ang), 0.25, dtype=F64)
+        R = M.moments(I, ang)
+        E = 0.25 * 4 * math.pi
+        ref = torch.tensor([E, 0, 0, 0, E / 3, 0, 0, E / 3, 0, E / 3], dtype=F64)
+        assert (R - ref).abs().max() < 1e-14
+
+
+def test_fluid_frame_energy_identity():
+    """R^{0bar 0bar} = sum Ihat (n^0bar)^2 dOmega (the E-bar of Sec. 2.5)."""
+    ang = GeodesicGrid(3)
+    rng = np.random.default_rng(4)
+    I = torch.tensor(rng.uniform(0, 1, (5, ang.n_ang)))
+    u = torch.tensor(rng.uniform(-0.5, 0.5, (5, 3)))
+    R = M.moments(I, ang, "fluid", u=u)
+    u0 = torch.sqrt(1 + (u * u).sum(-1))
+    nb = u0[:, None] - u @ ang.dir.T
+    assert (R[:, 0] - (I * nb ** 2 * ang.dOmega).sum(-1)).abs().max() < 1e-14
+    # the boost is a Lorentz transformation: eta-trace of R is invariant
+    Rt = M.moments(I, ang)
+    tr = lambda X: -X[:, 0] + X[:, 4] + X[:, 7] + X[:, 9]
+    assert (tr(R) - tr(Rt)).abs().max() < 1e-13
+    assert tr(Rt).abs().max() < 1e-14 * float(Rt[:, 0].max())    # null directions: traceless
+
+
+def test_coordinate_frame_in_cartesian_minkowski_is_tetrad_frame():
+    ang = GeodesicGrid(2)
+    I = torch.rand(3, ang.n_ang, dtype=F64)
+    e = torch.eye(4, dtype=F64).expand(3, 4, 4)
+    assert (M.moments(I, ang, "coord", e=e) - M.moments(I, ang)).abs().max() == 0.0
+
+
+def test_cfl_in_cartesian_minkowski():
+    ang = GeodesicGrid(2)
+    xf = [np.linspace(0, 1, 9), np.linspace(0, 2, 9), np.array([0.0, 1.0])]
+    st = Setup(Grid("mink_cart", 0.0, xf, (("periodic", "periodic"),) * 3, 2), ang)
+    ref = 0.3 * min(1 / 8 / float(ang.dir[:, 0].abs().max()), 2 / 8 / float(ang.dir[:, 1].abs().max()))
+    assert abs(CF.cfl_dt(st, 0.3) - ref) < 1e-15
+
+
+@pytest.fixture(scope="module")
+def adj_case():
+    w = W.make("adjoint2d", n=(6, 4, 1), level=1)
+    ang = GeodesicGrid(w["level"])
+    st = Setup(Grid(w["kind"], w["spin"], w["xf"], w["bc"], w["ndim"]), ang)
+    gas = {k: (torch.tensor(w[k]) if w[k] is not None else None)
+           for k in ("rho", "u", "alpha_a", "alpha_s", "eta")}
+    dt = CF.cfl_dt(st, 0.3)
+    return w, st, gas, dt
+
+
+def test_gradient_matches_central_differences(adj_case):
+    w, st, gas, dt = adj_case
+    opts = S.Opts(mode="emissivity")
+    I0, T0 = torch.tensor(w["I0"]), torch.tensor(w["T"])
+    nsteps = 3
+    L, grads = A.gradient(I0, T0, gas, dt, st, opts, nsteps)
+
+    def loss_with(field, cell, h):
+        g2 = {k: (v.clone() if v is not None else None) for k, v in gas.items()}
+        g2[field][cell] += h
+        I, T = I0, T0
+        for _ in range(nsteps):
+            I, T, _, _ = S.rk2_step(I, T, g2, dt, st, opts)
+        return float(A.loss_outer(I, st))
+
+    for fi, field in enumerate(("alpha_a", "alpha_s", "eta")):
+        for cell in [(0, 1, 5), (0, 2, 4), (0, 0, 3)]:
+            h = 1e-5 * float(gas[field][cell])
+            fd = (loss_with(field, cell, h) - loss_with(field, cell, -h)) / (2 * h)
+            ad = float(grads[fi][cell])
+            # relative to the gradient, floored at 1e-2 of its largest entry
+            # (below that the difference quotient is limited by roundoff)
+            assert abs(fd - ad) <= 1e-6 * max(abs(ad), 1e-2 * float(grads[fi].abs().max()))
+
+
+def test_step_vjp_dot_product(adj_case):
+    """<lambda, J delta> = <J^T lambda, delta> with J delta by forward-mode AD."""
+    w, st, gas, dt = adj_case
+    opts = S.Opts(mode="emissivity")
+    I0, T0 = torch.tensor(w["I0"]), torch.tensor(w["T"])
+    rng = np.random.default_rng(8)
+    lam = torch.tensor(rng.normal(size=I0.shape))
+    dI = torch.tensor(rng.normal(size=I0.shape))
+    da = torch.tensor(rng.normal(size=T0.shape))
+    lam_n, _, g_aa, _, _ = A.step_vjp(I0, T0, gas, dt, st, opts, lam)
+
+    def f(I, aa):
+        g2 = dict(gas)
+        g2["alpha_a"] = aa
+        return S.rk2_step(I, T0, g2, dt, st, opts)[0]
+
+    _, jvp = torch.func.jvp(f, (I0, gas["alpha_a"]), (dI, da))
+    lhs = float((lam * jvp).sum())
+    rhs = float((lam_n * dI).sum() + (g_aa * da).sum())
+    assert abs(lhs - rhs) < 1e-12 * max(abs(lhs), 1.0)

@@ -1,0 +1,159 @@
+"""Pins of the oracle's transport (Secs. 2.2-2.4, Eq. flux_space, Eq.
+flux_angle, Eq. radiation_integral) and of its RK2 step: exact invariants,
+exact beam speed, brute-force hand expansion and the hohlraum closed form
+(Sec. 3.4)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import step as S
+from oracle import transport as TR
+from oracle.angles import GeodesicGrid
+from oracle.transport import Grid, Setup
+
+F64 = torch.float64
+
+
+def cart_setup(n, level, ndim, L=1.0, bc="periodic"):
+    ang = GeodesicGrid(level)
+    xf = [np.linspace(0, L, n[d] + 1) if d < ndim else np.array([0.0, 1.0]) for d in range(3)]
+    grid = Grid("mink_cart", 0.0, xf, ((bc, bc),) * 3, ndim)
+    return Setup(grid, ang)
+
+
+@pytest.fixture(scope="module")
+def ks_setup():
+    ang = GeodesicGrid(2)
+    xf = [np.exp(np.linspace(math.log(1.6), math.log(8.0), 7)), np.linspace(0, math.pi, 7),
+          np.linspace(0, 2 * math.pi, 5)]
+    grid = Grid("ks_sph", 0.9, xf, (("outflow", "outflow"), ("polar", "polar"), ("periodic", "periodic")), 3)
+    return Setup(grid, ang)
+
+
+@pytest.mark.parametrize("recon", ["dc", "plm"])
+def test_uniform_field_is_stationary_in_flat_space(recon):
+    st = cart_setup((6, 5, 4), 2, 3)
+    I = torch.full(st.grid.shape + (st.ang.n_ang,), 0.37, dtype=F64)
+    L = S.operator_L(I, st, S.Opts(recon=recon))
+    assert L.abs().max() < 1e-14
+
+
+@pytest.mark.parametrize("recon", ["dc", "plm"])
+def test_conservation_periodic(recon):
+    """sum dV U is conserved to roundoff by the finite-volume form (Sec. 2.2)."""
+    st = cart_setup((6, 5, 4), 2, 3)
+    rng = np.random.default_rng(7)
+    I = torch.tensor(rng.uniform(0.5, 1.5, st.grid.shape + (st.ang.n_ang,)))
+    L = S.operator_L(I, st, S.Opts(recon=recon))
+    assert abs(float((L * st.dV[..., None]).sum())) < 1e-14 * float((I * st.dV[..., None]).sum())
+
+
+def test_angular_fluxes_conserve_per_cell(ks_setup):
+    rng = np.random.default_rng(3)
+    I = torch.tensor(rng.uniform(0.5, 1.5, ks_setup.grid.shape + (ks_setup.ang.n_ang,)))
+    divA = TR.angular_divergence(I, ks_setup)
+    tot = (divA * ks_setup.ang.dOmega).sum(-1)
+    assert tot.abs().max() < 1e-13 * float(divA.abs().max())
+    assert divA.abs().max() > 1e-3           # the fluxes are not trivially zero
+
+
+def test_no_angular_flux_in_cartesian_minkowski():
+    st = cart_setup((4, 4, 1), 2, 2)
+    I = torch.rand(st.grid.shape + (st.ang.n_ang,), dtype=F64)
+    assert TR.angular_divergence(I, st).abs().max() == 0.0
+
+
+def test_beam_centroid_moves_at_light_speed():
+    """DC upwind is conservative with a consistent linear flux, so the first
+    moment of a beam in one bin moves exactly at n^x / n^0 = nhat^x per unit
+    time (the RK2 integration of a linear first moment is exact)."""
+    st = cart_setup((64, 1, 1), 2, 1, L=1.0)
+    n = int(torch.argmax(st.ang.dir[:, 0]))
+    I = torch.zeros(st.grid.shape + (st.ang.n_ang,), dtype=F64)
+    I[0, 0, 10:20, n] = 1.0
+    x = torch.tensor(st.grid.xc[0])
+    opts = S.Opts(recon="dc", couple=False)
+    dt = 0.4 / 64
+    gas = None
+    t = 0.0
+    m0 = float((I[0, 0, :, n] * x).sum() / I[0, 0, :, n].sum())
+    for _ in range(20):
+        I, _, _, _ = S.rk2_step(I, torch.zeros(st.grid.shape, dtype=F64), gas, dt, st, opts)
+        t += dt
+    m1 = float((I[0, 0, :, n] * x).sum() / I[0, 0, :, n].sum())
+    assert abs((m1 - m0) - float(st.ang.dir[n, 0]) * t) < 1e-13
+    # other bins stay empty
+    others = torch.ones(st.ang.n_ang, dtype=torch.bool)
+    others[n] = False
+    assert I[..., others].abs().max() == 0.0
+
+
+def test_brute_force_two_cells_hand_expanded():
+    """2x1x1 periodic cells, level 1, DC: each face flux is -nhat^x I_upwind and
+    L_i = -(F_{i+1/2} - F_{i-1/2}) / dx, expanded by hand per bin."""
+    st = cart_setup((2, 1, 1), 1, 1, L=2.0)
+    rng = np.random.default_rng(1)
+    I = torch.tensor(rng.uniform(0.1, 1.0, (1, 1, 2, 12)))
+    L = S.operator_L(I, st, S.Opts(recon="dc"))
+    dx = 1.0
+    for n in range(12):
+        c = float(st.ang.dir[n, 0])
+        I0, I1 = float(I[0, 0, 0, n]), float(I[0, 0, 1, n])
+        # U = n^0 n_0 I = -I, flux of U through x faces = n^x n_0 I_up = -c I_up
+        up_left_face = I1 if c > 0 else I0     # face between cell 1 (periodic image) and cell 0
+        up_mid_face = I0 if c > 0 else I1
+        F_lo, F_mid = -c * up_left_face, -c * up_mid_face
+        assert abs(float(L[0, 0, 0, n]) + (F_mid - F_lo) / dx) < 1e-15
+        assert abs(float(L[0, 0, 1, n]) + (F_lo - F_mid) / dx) < 1e-15
+
+
+def test_plm_reproduces_linear_profile_slopes():
+    """van Leer's harmonic mean of equal one-sided differences is the difference itself."""
+    dl = torch.tensor([0.3, -0.2, 0.5, 0.0], dtype=F64)
+    dr = torch.tensor([0.3, -0.2, -0.1, 0.4], dtype=F64)
+    s = TR.van_leer(dl, dr)
+    assert torch.allclose(s, torch.tensor([0.3, -0.2, 0.0, 0.0], dtype=F64), atol=0, rtol=1e-15)
+
+
+def _hohlraum_error(level, ncell=64, t_end=0.5):
+    """1D hohlraum (Sec. 3.4): an isotropic wall of energy density 1 at x = 0."""
+    ang = GeodesicGrid(level)
+    xf = [np.linspace(0, 1, ncell + 1), np.array([0.0, 1.0]), np.array([0.0, 1.0])]
+    grid = Grid("mink_cart", 0.0, xf, (("outflow", "outflow"),) * 3, 1)
+    st = Setup(grid, ang)
+    I = torch.zeros(grid.shape + (ang.n_ang,), dtype=F64)
+    wall = 1.0 / (4 * math.pi)
+    dt = 0.4 / ncell
+    nsteps = int(round(t_end / dt))
+
+    def L(I):
+        Ie = TR.fill_ghosts(I, grid, ang.perm_pi2)
+        Ie[:, :, :TR.NG, :] = wall              # the wall held fixed
+        return -TR.spatial_divergence(Ie, st, "plm")
+
+    f = st.f
+    for _ in range(nsteps):
+        U0 = f * I
+        I1 = (U0 + dt * L(I)) / f
+        I = (0.5 * U0 + 0.5 * (f * I1 + dt * L(I1))) / f
+    t = nsteps * dt
+    x = torch.tensor(grid.xc[0])
+    xi = torch.clamp(x / t, max=1.0)
+    n4 = torch.cat([torch.ones(ang.n_ang, 1, dtype=F64), ang.dir], 1)
+    R = torch.einsum("kjin,nA,nB,n->iAB", I, n4, n4, ang.dOmega)
+    exact = [0.5 * (1 - xi), 0.25 * (1 - xi ** 2), (1 - xi ** 3) / 6.0]
+    dxx = 1.0 / ncell
+    eps = [float((R[:, 0, 0] - exact[0]).abs().sum() * dxx),
+           float((R[:, 0, 1] - exact[1]).abs().sum() * dxx),
+           float((R[:, 1, 1] - exact[2]).abs().sum() * dxx)]
+    return math.sqrt(sum(e * e for e in eps) / 3.0)
+
+
+def test_hohlraum_converges_in_angle():
+    """Sec. 3.4: R^tt = (1 - x/t)/2, R^tx = (1 - x^2/t^2)/4, R^xx = (1 - x^3/t^3)/6;
+    the error falls with the number of angles (about N_ang^(-1/2))."""
+    e = [_hohlraum_error(N) for N in (1, 2, 4)]
+    assert e[0] > e[1] > e[2]
+    assert e[2] < 0.03
