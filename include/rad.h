@@ -1,0 +1,199 @@
+/*
+ * rad.h -- C ABI of the GB300 finite-solid-angle GR radiation library.
+ *
+ * The library advances the gray specific intensity I(x, n) of White et al.,
+ * "General Relativistic Radiation with a Finite-Solid-Angle Method" (2023),
+ * on one logically rectangular block of cells held on one GPU:
+ *   - Sec. 2.6:      geodesic angle grid (rad_init_angles, rad_get_angles)
+ *   - Secs. 2.1-2.2: metric, normal-observer tetrad, Ricci rotation
+ *                    coefficients, exact cell volumes (rad_set_metric)
+ *   - Secs. 2.3-2.4, Eq. radiation_integral: reconstruction, upwind spatial
+ *                    and angular fluxes, flux divergence (rad_step)
+ *   - Sec. 2.5:      locally implicit coupling via a quartic for T (rad_step)
+ *   - Sec. 2.4:      n0crit guard (rad_step)
+ *   - Sec. 2.5:      R^{mu nu} = sum I n^mu n^nu dOmega (rad_moments)
+ *   - gradient of an outgoing-flux loss through a step (rad_step_adjoint,
+ *     rad_loss_outer)
+ *
+ * Conventions shared by every call
+ *   - Status: every int-returning call returns RAD_OK (0) or a negative
+ *     rad_status.  rad_last_error() gives a message for the last failure of
+ *     that context.  No C++ exception crosses this interface.
+ *   - Memory: the caller owns every buffer it passes (device pointers unless
+ *     stated "host"), contiguous, at least 16-byte aligned; the library
+ *     never frees them.  The context owns its tables and scratch.
+ *   - Streams: all device work is enqueued on the stream given to
+ *     rad_create (NULL = legacy default stream).  Calls are asynchronous
+ *     except rad_init_angles, rad_get_angles, rad_set_metric, rad_cfl_dt and
+ *     rad_check, which synchronise that stream.
+ *   - Device errors (non-finite intensity, unbracketed quartic, divergent
+ *     Newton iteration) set a sticky error word in device memory instead of
+ *     trapping; rad_check reads and clears it.
+ *   - Intensity layout: I[k][j][i][n] for k < n[2], j < n[1], i < n[0],
+ *     n < n_ang_padded (angle fastest).  Bins n >= n_ang are padding: never
+ *     read as data and never written.  Element type is double (RAD_F64) or
+ *     float (RAD_F32).  There are no ghost cells in the array: boundary
+ *     conditions are applied by index mapping when neighbours are read.
+ *   - Coordinates are (x1, x2, x3); for spherical metrics (r, theta, phi).
+ */
+#ifndef RAD_H
+#define RAD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rad_ctx rad_ctx;
+
+typedef enum {
+  RAD_OK = 0,
+  RAD_EINVAL = -1,        /* bad argument (checked on the host, nothing enqueued) */
+  RAD_ENOMEM = -2,        /* device or host allocation failed */
+  RAD_ECUDA = -3,         /* a CUDA runtime call failed */
+  RAD_ENOCONV = -4,       /* quartic without a bracketed root / Newton cap hit */
+  RAD_ENONFINITE = -5,    /* a non-finite intensity or temperature was produced */
+  RAD_ESTATE = -6,        /* call out of order (e.g. step before set_metric) */
+  RAD_EUNSUPPORTED = -7   /* valid request this build does not implement */
+} rad_status;
+
+enum { RAD_MINK_CART = 0, RAD_MINK_SPH = 1, RAD_KS_SPH = 2 };
+enum { RAD_BC_PERIODIC = 0, RAD_BC_OUTFLOW = 1, RAD_BC_POLAR = 2 };
+enum { RAD_F64 = 0, RAD_F32 = 1 };
+enum { RAD_RECON_DC = 0, RAD_RECON_PLM = 1 };
+enum { RAD_COUPLE_THERMAL = 0, RAD_COUPLE_EMISSIVITY = 1, RAD_COUPLE_NONE = 2 };
+enum { RAD_FRAME_TETRAD = 0, RAD_FRAME_COORD = 1, RAD_FRAME_FLUID = 2 };
+enum { RAD_MOM_SIMT = 0, RAD_MOM_BF16X3 = 1 };
+
+/* Create a context bound to a CUDA stream (cudaStream_t passed as void*). */
+int rad_create(rad_ctx **out, void *cuda_stream);
+/* Free the context, its tables and scratch.  NULL is ignored. */
+void rad_destroy(rad_ctx *ctx);
+/* Message of the last failing call on ctx ("" if none).  Owned by ctx. */
+const char *rad_last_error(const rad_ctx *ctx);
+
+/*
+ * Build the level-N geodesic angle grid (Sec. 2.6: icosahedron, faces cut
+ * flat into N^2 triangles, cells around the lattice vertices bounded by
+ * great-circle arcs through the projected triangle centroids).
+ * n_ang = 10 N^2 + 2; n_ang_padded rounds it up to a multiple of 4.
+ * Orientation: a pentagon centred on +3hat, the 2hat axis a two-fold axis.
+ * level must be in [1, 32].  Synchronous; replaces any previous grid (and
+ * invalidates the metric, which must be set again).
+ */
+int rad_init_angles(rad_ctx *ctx, int level, int *n_ang_out, int *n_ang_padded_out);
+
+/*
+ * Copy the grid to host arrays (each may be NULL):
+ *   dir[n_ang][3] unit directions (components on 1hat, 2hat, 3hat),
+ *   dOmega[n_ang] exact spherical-polygon solid angles (sum 4 pi),
+ *   nbr[n_ang][6] neighbour bins, -1 padding for the 12 pentagons.
+ */
+int rad_get_angles(rad_ctx *ctx, double *dir, double *dOmega, int *nbr);
+
+typedef struct {
+  int kind;        /* RAD_MINK_CART, RAD_MINK_SPH or RAD_KS_SPH */
+  double spin;     /* Kerr spin a (M = 1), |a| < 1; ignored for flat space */
+} rad_metric;
+
+typedef struct {
+  int ndim;               /* dimensions carrying fluxes: 1, 2 or 3 */
+  int n[3];               /* cells per dimension; n[d] = 1 for d >= ndim */
+  const double *xf[3];    /* host face coordinates, n[d] + 1 increasing values;
+                             xf[2] must be uniformly spaced */
+  int bc_lo[3], bc_hi[3]; /* RAD_BC_*; polar only on x2 of a spherical metric,
+                             which then needs theta faces at 0 / pi and an even
+                             n[2] (or n[2] = 1) covering 2 pi in phi */
+} rad_grid;
+
+/*
+ * Compute the per-cell and per-face geometry in FP64 (Secs. 2.1-2.2):
+ * metric, normal-observer tetrad (Cartesian: identity; spherical:
+ * theta -> 3hat, phi -> 1hat, r -> 2hat by Gram-Schmidt), Ricci rotation
+ * coefficients (Eq. ricci) from exact forward-mode derivatives, exact
+ * Delta V and Delta A.  Requires rad_init_angles.  Synchronous.
+ */
+int rad_set_metric(rad_ctx *ctx, const rad_metric *metric, const rad_grid *grid);
+
+/* Gas state: device FP64 arrays over active cells, [k][j][i] (u: [k][j][i][3]). */
+typedef struct {
+  const double *rho;      /* rest-mass density (c_v = rho / (Gamma - 1)) */
+  const double *u;        /* fluid four-velocity u^ihat in the tetrad frame */
+  const double *alpha_a;  /* fluid-frame absorption coefficient (alpha_P = alpha_a) */
+  const double *alpha_s;  /* fluid-frame scattering coefficient */
+  const double *eta;      /* fluid-frame emissivity; only for RAD_COUPLE_EMISSIVITY */
+  double *T;              /* gas temperature, updated in place by rad_step */
+} rad_gas;
+
+typedef struct {
+  int precision;     /* RAD_F64 or RAD_F32: element type of I and of the
+                        per-angle transport / coupling arithmetic; the
+                        geometry, the quartic and the temperature are FP64 */
+  int recon;         /* RAD_RECON_DC or RAD_RECON_PLM (van Leer) */
+  int coupling;      /* RAD_COUPLE_THERMAL, _EMISSIVITY or _NONE */
+  double n0crit;     /* guard threshold on |n_0| (Sec. 2.4), default 0.1 */
+  int zero_guard;    /* apply the guard (default 1) */
+  double a_rad;      /* radiation constant, default 1 */
+  double gamma;      /* adiabatic index, default 5/3 */
+} rad_opts;
+
+/* Fill *opts with the defaults above (FP64, PLM, thermal coupling). */
+void rad_opts_default(rad_opts *opts);
+
+/*
+ * dt = cfl * min(dt_space, dt_angle): dt_space = min over cells, flux
+ * dimensions and bins of dx^d / |n^d / n^0|; dt_angle = min over cells and
+ * bins of dOmega n^0 / sum_edges l_e |V . nu_e|.  Synchronous.
+ */
+int rad_cfl_dt(rad_ctx *ctx, double cfl, double *dt_out);
+
+/*
+ * One SSP-RK2 step of Eq. radiation_integral with the Sec. 2.5 coupling
+ * after each stage (dt, then dt/2; the gas T entering stage 2 is the
+ * average of T before and after stage 1) and the n0crit guard after each
+ * coupling.  I (device, layout above) and gas->T are updated in place.
+ * gas_src (device [k][j][i][4], nullable) receives -(dR^1/2 + dR^2), the
+ * RK-weighted change of R^0_mu from the two couplings (the gas's share).
+ * Allocates its stage scratch (one intensity array) on first use.
+ */
+int rad_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt,
+             const rad_opts *opts, double *gas_src);
+
+/*
+ * Moments R^{AB} = sum_n I_n n^A n^B dOmega_n of every cell, written as 10
+ * components [cell][10] in the order 00 01 02 03 11 12 13 22 23 33.
+ * precision: element type of I (and of R for RAD_MOM_BF16X3, which writes
+ * float).  frame: tetrad, coordinate (e e R) or fluid (Lambda Lambda R,
+ * needs gas->u).  method: RAD_MOM_SIMT (CUDA cores, I's precision) or
+ * RAD_MOM_BF16X3 (RAD_F32 only: tensor cores, I and the weights split into
+ * bf16 hi + lo, three products, FP32 accumulation).
+ */
+int rad_moments(rad_ctx *ctx, const void *I, int precision, int frame, int method,
+                const rad_gas *gas, void *R);
+
+/*
+ * Reverse-mode step: given the state I_n (checkpoint, not modified) and the
+ * adjoint lam_np1 = dL/dI_{n+1}, write lam_n = dL/dI_n and ACCUMULATE
+ * (+=) dL/dalpha_a, dL/dalpha_s, dL/deta (device FP64 [k][j][i]) through
+ * the step rad_step would take from I_n.  opts->coupling must be
+ * RAD_COUPLE_EMISSIVITY or RAD_COUPLE_NONE (T frozen).  lam arrays use the
+ * intensity layout and precision.  g_eta may be NULL.
+ */
+int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
+                     const rad_opts *opts, const void *lam_np1, void *lam_n,
+                     double *g_alpha_a, double *g_alpha_s, double *g_eta);
+
+/*
+ * Outgoing-flux loss L = sum_{k,j} sum_{n: n^1 > 0 at the outer x1 face}
+ * I[k][j][n1-1][n] dOmega_n, written to *L_dev (device double); if dL_dI is
+ * not NULL it receives dL/dI (the seed of rad_step_adjoint).
+ */
+int rad_loss_outer(rad_ctx *ctx, const void *I, int precision, double *L_dev, void *dL_dI);
+
+/* Read and clear the sticky device error word.  Synchronous.  Returns
+ * RAD_OK or the first recorded rad_status. */
+int rad_check(rad_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAD_H */

@@ -85,14 +85,18 @@ def couple(I, T, gas, dt, setup, a_rad=1.0, gamma=5.0 / 3.0, mode="thermal"):
     den = n0 + nbar0 * aE * dt
     c1 = n0 / den
     c2 = nbar0 * dt / (FOUR_PI * den)
-    A1 = (c1 * Ibar * dOmbar).sum(-1)
     A2 = dt / FOUR_PI * (nbar0 / den * dOmbar).sum(-1)
     Em = (Ibar * dOmbar).sum(-1)
+    # A1 - Ebar- as one integral of (c1 - 1) Ibar dOmega_bar (c1 - 1 =
+    # -n^0bar alpha_E dt / den): the same quantity as the difference of the
+    # two integrals, without its cancellation when alpha_E dt << 1
+    D = (-(nbar0 * aE * dt) / den * Ibar * dOmbar).sum(-1)
+    A1 = D + Em
     if mode == "thermal":
         cv = gas["rho"] / (gamma - 1.0)
         B4 = A2 * aa * a_rad
         B1 = cv * (1.0 - A2 * a_s)
-        B0 = A1 - B1 * T - (1.0 - A2 * a_s) * Em
+        B0 = D + A2 * a_s * Em - B1 * T            # = A1 - B1 T- - (1 - A2 alpha_s) Ebar-
         Tp, ok = quartic_root(B4, B1, B0)
         Ep = Em - cv * (Tp - T)
         S = aa * a_rad * Tp ** 4 + a_s * Ep

@@ -1,0 +1,232 @@
+// Geodesic angle grid builder (host, FP64), Sec. 2.6.
+//
+// Construction: the 12 vertices of an icosahedron (one on +3hat, the upper
+// ring of five at azimuths 2 pi k / 5, the lower ring offset by pi / 5, so
+// that the 2hat axis is a two-fold axis); its 20 faces are found as the
+// vertex triples at mutual edge distance.  Each face is cut flat into N^2
+// triangles on the barycentric lattice a + b + c = N.  Lattice points are
+// identified exactly (no floating tolerance) by their integer weights on
+// the icosahedron vertices, so points shared by neighbouring faces merge.
+// The radiation directions are the projected lattice points; the cell of a
+// point is bounded by great-circle arcs through the projected centroids of
+// the lattice triangles around it.  Solid angles are sums of
+// Van Oosterom-Strackee triangle areas over the fan from the cell centre.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <map>
+
+#include "rad_internal.h"
+
+namespace rad {
+namespace {
+
+struct V3 {
+  double x, y, z;
+};
+inline V3 add(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+inline V3 sub(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+inline V3 mul(V3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
+inline double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+inline double norm(V3 a) { return std::sqrt(dot(a, a)); }
+inline V3 unit(V3 a) { return mul(a, 1.0 / norm(a)); }
+
+// Solid angle of the spherical triangle (a, b, c) of unit vectors
+// (Van Oosterom & Strackee 1983).
+double vos_area(V3 a, V3 b, V3 c) {
+  double num = std::fabs(dot(a, cross(b, c)));
+  double den = 1.0 + dot(a, b) + dot(b, c) + dot(c, a);
+  return 2.0 * std::atan2(num, den);
+}
+
+// Exact identity of a lattice point: sorted (vertex, weight) pairs.
+uint64_t lattice_key(std::array<std::pair<int, int>, 3> w) {
+  std::sort(w.begin(), w.end());
+  uint64_t key = 0;
+  for (auto &p : w) {
+    if (p.second == 0) continue;
+    key = key * 1024u + (uint64_t)(p.first * 64 + p.second);
+  }
+  return key;
+}
+
+}  // namespace
+
+bool build_geodesic(int N, AngleGrid &g, std::string &err) {
+  if (N < 1 || N > 32) {
+    err = "geodesic level must be in [1, 32]";
+    return false;
+  }
+  // icosahedron
+  std::vector<V3> ico;
+  const double h = 1.0 / std::sqrt(5.0), r = 2.0 / std::sqrt(5.0);
+  ico.push_back({0.0, 0.0, 1.0});
+  for (int k = 0; k < 5; ++k) {
+    double psi = 2.0 * kPi * k / 5.0;
+    ico.push_back({r * std::cos(psi), r * std::sin(psi), h});
+  }
+  for (int k = 0; k < 5; ++k) {
+    double psi = 2.0 * kPi * k / 5.0 + kPi / 5.0;
+    ico.push_back({r * std::cos(psi), r * std::sin(psi), -h});
+  }
+  ico.push_back({0.0, 0.0, -1.0});
+  double edge2 = 1e9;
+  for (int a = 0; a < 12; ++a)
+    for (int b = a + 1; b < 12; ++b) edge2 = std::min(edge2, dot(sub(ico[a], ico[b]), sub(ico[a], ico[b])));
+  auto adjacent = [&](int a, int b) {
+    V3 d = sub(ico[a], ico[b]);
+    return std::fabs(dot(d, d) - edge2) < 1e-9;
+  };
+  std::vector<std::array<int, 3>> faces;
+  for (int a = 0; a < 12; ++a)
+    for (int b = a + 1; b < 12; ++b)
+      for (int c = b + 1; c < 12; ++c)
+        if (adjacent(a, b) && adjacent(b, c) && adjacent(a, c)) faces.push_back({a, b, c});
+  if (faces.size() != 20) {
+    err = "icosahedron face search failed";
+    return false;
+  }
+
+  std::map<uint64_t, int> ids;
+  std::vector<V3> flat;                   // unprojected lattice points
+  std::vector<std::array<int, 3>> tris;   // lattice triangles
+  std::vector<V3> tri_centroid;           // projected centroids (polygon corners)
+  for (auto &f : faces) {
+    auto point = [&](int a, int b) {
+      int c = N - a - b;
+      V3 p = add(add(mul(ico[f[0]], a), mul(ico[f[1]], b)), mul(ico[f[2]], c));
+      return mul(p, 1.0 / N);
+    };
+    auto id = [&](int a, int b) {
+      int c = N - a - b;
+      uint64_t key = lattice_key({std::make_pair(f[0], a), std::make_pair(f[1], b), std::make_pair(f[2], c)});
+      auto it = ids.find(key);
+      if (it != ids.end()) return it->second;
+      int n = (int)flat.size();
+      ids[key] = n;
+      flat.push_back(point(a, b));
+      return n;
+    };
+    for (int a = 0; a <= N; ++a)
+      for (int b = 0; a + b <= N; ++b) {
+        int c = N - a - b;
+        if (c >= 1) {
+          tris.push_back({id(a, b), id(a + 1, b), id(a, b + 1)});
+          tri_centroid.push_back(unit(add(add(point(a, b), point(a + 1, b)), point(a, b + 1))));
+        }
+        if (c >= 2) {
+          tris.push_back({id(a + 1, b), id(a, b + 1), id(a + 1, b + 1)});
+          tri_centroid.push_back(unit(add(add(point(a + 1, b), point(a, b + 1)), point(a + 1, b + 1))));
+        }
+      }
+  }
+  const int n_ang = (int)flat.size();
+  if (n_ang != 10 * N * N + 2 || (int)tris.size() != 20 * N * N) {
+    err = "geodesic grid has the wrong cell count";
+    return false;
+  }
+  std::vector<V3> dir(n_ang);
+  for (int n = 0; n < n_ang; ++n) dir[n] = unit(flat[n]);
+
+  // triangles around vertices and the two triangles of each lattice edge
+  std::vector<std::vector<int>> vtris(n_ang);
+  std::map<std::pair<int, int>, std::vector<int>> etris;
+  for (int t = 0; t < (int)tris.size(); ++t) {
+    for (int k = 0; k < 3; ++k) {
+      vtris[tris[t][k]].push_back(t);
+      int p = tris[t][k], q = tris[t][(k + 1) % 3];
+      etris[{std::min(p, q), std::max(p, q)}].push_back(t);
+    }
+  }
+  if ((int)etris.size() != 30 * N * N) {
+    err = "geodesic grid has the wrong edge count";
+    return false;
+  }
+
+  g = AngleGrid();
+  g.level = N;
+  g.n_ang = n_ang;
+  g.n_ap = (n_ang + 3) / 4 * 4;
+  g.dir.resize(3 * n_ang);
+  g.dOmega.resize(n_ang);
+  for (int n = 0; n < n_ang; ++n) {
+    g.dir[3 * n] = dir[n].x;
+    g.dir[3 * n + 1] = dir[n].y;
+    g.dir[3 * n + 2] = dir[n].z;
+    // order the corners by angle in the tangent plane, then sum the fan
+    V3 c = dir[n];
+    V3 t1 = unit(cross(c, V3{0.3, 0.5, 0.7}));
+    V3 t2 = cross(c, t1);
+    std::vector<std::pair<double, V3>> cs;
+    for (int t : vtris[n]) {
+      V3 p = tri_centroid[t];
+      cs.push_back({std::atan2(dot(p, t2), dot(p, t1)), p});
+    }
+    std::sort(cs.begin(), cs.end(), [](const std::pair<double, V3> &a, const std::pair<double, V3> &b) {
+      return a.first < b.first;
+    });
+    double area = 0.0;
+    for (size_t k = 0; k < cs.size(); ++k) area += vos_area(c, cs[k].second, cs[(k + 1) % cs.size()].second);
+    g.dOmega[n] = area;
+  }
+
+  g.n_edge = (int)etris.size();
+  g.nbr.assign(6 * n_ang, -1);
+  g.slot_edge.assign(6 * n_ang, -1);
+  std::vector<std::vector<std::pair<int, int>>> nb(n_ang);
+  int e = 0;
+  for (auto &kv : etris) {
+    int p = kv.first.first, q = kv.first.second;
+    V3 c1 = tri_centroid[kv.second[0]], c2 = tri_centroid[kv.second[1]];
+    V3 cr = cross(c1, c2);
+    double len = std::atan2(norm(cr), dot(c1, c2));
+    V3 mid = unit(add(c1, c2));
+    V3 nu = unit(cr);
+    if (dot(nu, sub(dir[q], dir[p])) < 0.0) nu = mul(nu, -1.0);
+    g.edge_pq.push_back(p);
+    g.edge_pq.push_back(q);
+    g.edge_mid.insert(g.edge_mid.end(), {mid.x, mid.y, mid.z});
+    g.edge_nrm.insert(g.edge_nrm.end(), {nu.x, nu.y, nu.z});
+    g.edge_len.push_back(len);
+    nb[p].push_back({q, e});
+    nb[q].push_back({p, e});
+    ++e;
+  }
+  for (int n = 0; n < n_ang; ++n) {
+    std::sort(nb[n].begin(), nb[n].end());
+    if (nb[n].size() < 5 || nb[n].size() > 6) {
+      err = "geodesic cell with an unexpected number of neighbours";
+      return false;
+    }
+    for (size_t s = 0; s < nb[n].size(); ++s) {
+      g.nbr[6 * n + s] = nb[n][s].first;
+      g.slot_edge[6 * n + s] = nb[n][s].second;
+    }
+  }
+  // bin of the direction rotated by pi about 2hat: (x, y, z) -> (-x, y, -z)
+  g.perm.assign(n_ang, -1);
+  for (int n = 0; n < n_ang; ++n) {
+    V3 rd = {-dir[n].x, dir[n].y, -dir[n].z};
+    int best = -1;
+    double bd = 1e9;
+    for (int m = 0; m < n_ang; ++m) {
+      V3 d = sub(rd, dir[m]);
+      double dd = dot(d, d);
+      if (dd < bd) {
+        bd = dd;
+        best = m;
+      }
+    }
+    if (bd > 1e-24) {
+      err = "angle grid is not symmetric under the pi rotation about 2hat";
+      return false;
+    }
+    g.perm[n] = best;
+  }
+  return true;
+}
+
+}  // namespace rad

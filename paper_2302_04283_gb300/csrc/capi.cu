@@ -1,0 +1,331 @@
+// C ABI entry points: argument validation, context state, table upload and
+// dispatch to the kernels.  No exception crosses this boundary.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "rad_internal.h"
+
+using rad::AngleGrid;
+
+namespace {
+
+int fail(rad_ctx *ctx, int code, const std::string &msg) {
+  if (ctx) ctx->last_error = msg;
+  return code;
+}
+
+void free_angles(rad::DevAngles &d) {
+  cudaFree(d.dir);
+  cudaFree(d.dOmega);
+  cudaFree(d.slot_nbr);
+  cudaFree(d.slot_edge);
+  cudaFree(d.perm);
+  cudaFree(d.edge_geo);
+  cudaFree(d.edge_pq);
+  d = rad::DevAngles();
+}
+
+template <typename T>
+cudaError_t upload(T **dst, const std::vector<T> &src, cudaStream_t st) {
+  cudaError_t e = cudaMalloc(dst, src.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int rad_create(rad_ctx **out, void *cuda_stream) {
+  if (!out) return RAD_EINVAL;
+  *out = nullptr;
+  rad_ctx *c = new (std::nothrow) rad_ctx();
+  if (!c) return RAD_ENOMEM;
+  c->stream = (cudaStream_t)cuda_stream;
+  if (cudaMalloc(&c->err_word, sizeof(int)) != cudaSuccess) {
+    delete c;
+    return RAD_ENOMEM;
+  }
+  cudaMemsetAsync(c->err_word, 0, sizeof(int), c->stream);
+  *out = c;
+  return RAD_OK;
+}
+
+void rad_destroy(rad_ctx *ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  free_angles(ctx->dang);
+  rad::free_geometry(ctx->geom);
+  cudaFree(ctx->err_word);
+  cudaFree(ctx->scratch_I);
+  cudaFree(ctx->scratch_T);
+  cudaFree(ctx->adj_buf);
+  cudaFree(ctx->wt_dev);
+  delete ctx;
+}
+
+const char *rad_last_error(const rad_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+void rad_opts_default(rad_opts *o) {
+  if (!o) return;
+  o->precision = RAD_F64;
+  o->recon = RAD_RECON_PLM;
+  o->coupling = RAD_COUPLE_THERMAL;
+  o->n0crit = 0.1;
+  o->zero_guard = 1;
+  o->a_rad = 1.0;
+  o->gamma = 5.0 / 3.0;
+}
+
+int rad_init_angles(rad_ctx *ctx, int level, int *n_ang_out, int *n_ang_padded_out) {
+  if (!ctx) return RAD_EINVAL;
+  AngleGrid g;
+  std::string err;
+  if (!rad::build_geodesic(level, g, err)) return fail(ctx, RAD_EINVAL, err);
+  cudaStreamSynchronize(ctx->stream);
+  free_angles(ctx->dang);
+  cudaFree(ctx->wt_dev);
+  ctx->wt_dev = nullptr;
+  ctx->have_angles = ctx->have_metric = false;
+  // device tables, padded to n_ap bins with zero directions / solid angles
+  std::vector<double> dir(3 * g.n_ap, 0.0), dOm(g.n_ap, 0.0), egeo(8 * g.n_edge, 0.0);
+  std::vector<int> snb(6 * g.n_ap, -1), sed(6 * g.n_ap, -1), perm(g.n_ap, 0);
+  for (int n = 0; n < g.n_ang; ++n) {
+    for (int a = 0; a < 3; ++a) dir[3 * n + a] = g.dir[3 * n + a];
+    dOm[n] = g.dOmega[n];
+    for (int s = 0; s < 6; ++s) {
+      snb[6 * n + s] = g.nbr[6 * n + s];
+      sed[6 * n + s] = g.slot_edge[6 * n + s];
+    }
+    perm[n] = g.perm[n];
+  }
+  for (int e = 0; e < g.n_edge; ++e) {
+    for (int a = 0; a < 3; ++a) {
+      egeo[8 * e + a] = g.edge_mid[3 * e + a];
+      egeo[8 * e + 3 + a] = g.edge_nrm[3 * e + a];
+    }
+    egeo[8 * e + 6] = g.edge_len[e];
+    egeo[8 * e + 7] = g.edge_pq[2 * e];
+  }
+  cudaError_t ce;
+  if ((ce = upload(&ctx->dang.dir, dir, ctx->stream)) != cudaSuccess ||
+      (ce = upload(&ctx->dang.dOmega, dOm, ctx->stream)) != cudaSuccess ||
+      (ce = upload(&ctx->dang.slot_nbr, snb, ctx->stream)) != cudaSuccess ||
+      (ce = upload(&ctx->dang.slot_edge, sed, ctx->stream)) != cudaSuccess ||
+      (ce = upload(&ctx->dang.perm, perm, ctx->stream)) != cudaSuccess ||
+      (ce = upload(&ctx->dang.edge_geo, egeo, ctx->stream)) != cudaSuccess ||
+      (ce = upload(&ctx->dang.edge_pq, g.edge_pq, ctx->stream)) != cudaSuccess) {
+    free_angles(ctx->dang);
+    return fail(ctx, RAD_ENOMEM, std::string("angle table upload failed: ") + cudaGetErrorString(ce));
+  }
+  if ((ce = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+    return fail(ctx, RAD_ECUDA, std::string("angle table upload failed: ") + cudaGetErrorString(ce));
+  ctx->ang = std::move(g);
+  ctx->have_angles = true;
+  if (n_ang_out) *n_ang_out = ctx->ang.n_ang;
+  if (n_ang_padded_out) *n_ang_padded_out = ctx->ang.n_ap;
+  return RAD_OK;
+}
+
+int rad_get_angles(rad_ctx *ctx, double *dir, double *dOmega, int *nbr) {
+  if (!ctx) return RAD_EINVAL;
+  if (!ctx->have_angles) return fail(ctx, RAD_ESTATE, "rad_init_angles has not been called");
+  const AngleGrid &g = ctx->ang;
+  if (dir) std::memcpy(dir, g.dir.data(), g.dir.size() * sizeof(double));
+  if (dOmega) std::memcpy(dOmega, g.dOmega.data(), g.dOmega.size() * sizeof(double));
+  if (nbr) std::memcpy(nbr, g.nbr.data(), g.nbr.size() * sizeof(int));
+  return RAD_OK;
+}
+
+int rad_set_metric(rad_ctx *ctx, const rad_metric *m, const rad_grid *gr) {
+  if (!ctx) return RAD_EINVAL;
+  if (!m || !gr) return fail(ctx, RAD_EINVAL, "null metric or grid");
+  if (!ctx->have_angles) return fail(ctx, RAD_ESTATE, "rad_init_angles must precede rad_set_metric");
+  if (m->kind < RAD_MINK_CART || m->kind > RAD_KS_SPH) return fail(ctx, RAD_EINVAL, "unknown metric kind");
+  if (m->kind == RAD_KS_SPH && !(std::fabs(m->spin) < 1.0)) return fail(ctx, RAD_EINVAL, "|spin| must be < 1");
+  if (gr->ndim < 1 || gr->ndim > 3) return fail(ctx, RAD_EINVAL, "ndim must be 1, 2 or 3");
+  for (int d = 0; d < 3; ++d) {
+    if (gr->n[d] < 1) return fail(ctx, RAD_EINVAL, "cell counts must be >= 1");
+    if (d >= gr->ndim && gr->n[d] != 1) return fail(ctx, RAD_EINVAL, "n[d] must be 1 beyond ndim");
+    if (!gr->xf[d]) return fail(ctx, RAD_EINVAL, "null face coordinates");
+    for (int t = 0; t < gr->n[d]; ++t)
+      if (!(gr->xf[d][t + 1] > gr->xf[d][t])) return fail(ctx, RAD_EINVAL, "face coordinates must increase");
+    for (int s = 0; s < 2; ++s) {
+      int bc = s ? gr->bc_hi[d] : gr->bc_lo[d];
+      if (bc < RAD_BC_PERIODIC || bc > RAD_BC_POLAR) return fail(ctx, RAD_EINVAL, "unknown boundary kind");
+      if (bc == RAD_BC_POLAR && (d != 1 || m->kind == RAD_MINK_CART))
+        return fail(ctx, RAD_EINVAL, "polar boundaries apply to theta (x2) of a spherical metric only");
+    }
+    if ((gr->bc_lo[d] == RAD_BC_PERIODIC) != (gr->bc_hi[d] == RAD_BC_PERIODIC))
+      return fail(ctx, RAD_EINVAL, "periodic boundaries must be set on both sides");
+  }
+  const double *x3 = gr->xf[2];
+  double w3 = x3[1] - x3[0];
+  for (int t = 1; t < gr->n[2]; ++t)
+    if (std::fabs((x3[t + 1] - x3[t]) - w3) > 1e-12 * std::fabs(w3))
+      return fail(ctx, RAD_EUNSUPPORTED, "x3 faces must be uniformly spaced");
+  bool polar = gr->bc_lo[1] == RAD_BC_POLAR || gr->bc_hi[1] == RAD_BC_POLAR;
+  if (polar) {
+    if (gr->n[1] < 2) return fail(ctx, RAD_EINVAL, "polar boundaries need n[1] >= 2");
+    if (gr->n[2] > 1 && (gr->n[2] % 2 != 0)) return fail(ctx, RAD_EINVAL, "polar boundaries need an even n[2]");
+    if (std::fabs((x3[gr->n[2]] - x3[0]) - 2.0 * rad::kPi) > 1e-9)
+      return fail(ctx, RAD_EINVAL, "polar boundaries need x3 to span 2 pi");
+    if (gr->bc_lo[1] == RAD_BC_POLAR && std::fabs(gr->xf[1][0]) > 1e-12)
+      return fail(ctx, RAD_EINVAL, "polar boundary at x2 lo needs theta = 0");
+    if (gr->bc_hi[1] == RAD_BC_POLAR && std::fabs(gr->xf[1][gr->n[1]] - rad::kPi) > 1e-12)
+      return fail(ctx, RAD_EINVAL, "polar boundary at x2 hi needs theta = pi");
+  }
+  if (m->kind != RAD_MINK_CART) {
+    if (!(gr->xf[0][0] > 0.0)) return fail(ctx, RAD_EINVAL, "r must be positive");
+    if (gr->xf[1][0] < 0.0 || gr->xf[1][gr->n[1]] > rad::kPi + 1e-12) return fail(ctx, RAD_EINVAL, "theta outside [0, pi]");
+    if (m->kind == RAD_KS_SPH) {
+      double rh = 1.0 + std::sqrt(1.0 - m->spin * m->spin);
+      (void)rh;   // Kerr-Schild coordinates are regular through the horizon
+    }
+  }
+  rad::DevGeom &G = ctx->geom;
+  G.kind = m->kind;
+  G.spin = m->kind == RAD_KS_SPH ? m->spin : 0.0;
+  G.ndim = gr->ndim;
+  for (int d = 0; d < 3; ++d) {
+    G.n[d] = gr->n[d];
+    G.bc_lo[d] = gr->bc_lo[d];
+    G.bc_hi[d] = gr->bc_hi[d];
+    G.xf[d].assign(gr->xf[d], gr->xf[d] + gr->n[d] + 1);
+  }
+  std::string err;
+  ctx->have_metric = false;
+  int st = rad::compute_geometry(ctx, err);
+  if (st != RAD_OK) return fail(ctx, st, err);
+  ctx->have_metric = true;
+  return RAD_OK;
+}
+
+int rad_cfl_dt(rad_ctx *ctx, double cfl, double *dt_out) {
+  if (!ctx) return RAD_EINVAL;
+  if (!dt_out || !(cfl > 0.0)) return fail(ctx, RAD_EINVAL, "cfl must be > 0 and dt_out non-null");
+  if (!ctx->have_metric) return fail(ctx, RAD_ESTATE, "rad_set_metric has not been called");
+  std::string err;
+  int st = rad::launch_cfl(ctx, cfl, dt_out, err);
+  return st == RAD_OK ? st : fail(ctx, st, err);
+}
+
+static int check_gas(rad_ctx *ctx, const rad_gas *gas, const rad_opts *o, bool need_T) {
+  if (!gas) return fail(ctx, RAD_EINVAL, "null gas");
+  if (o->coupling != RAD_COUPLE_NONE) {
+    if (!gas->rho || !gas->u || !gas->alpha_a || !gas->alpha_s)
+      return fail(ctx, RAD_EINVAL, "gas fields rho, u, alpha_a, alpha_s are required for coupling");
+    if (o->coupling == RAD_COUPLE_EMISSIVITY && !gas->eta)
+      return fail(ctx, RAD_EINVAL, "emissivity coupling needs gas->eta");
+  }
+  if (need_T && !gas->T) return fail(ctx, RAD_EINVAL, "gas->T is required");
+  return RAD_OK;
+}
+
+static int check_opts(rad_ctx *ctx, const rad_opts *o) {
+  if (!o) return fail(ctx, RAD_EINVAL, "null opts");
+  if (o->precision != RAD_F64 && o->precision != RAD_F32) return fail(ctx, RAD_EINVAL, "bad precision");
+  if (o->recon != RAD_RECON_DC && o->recon != RAD_RECON_PLM) return fail(ctx, RAD_EINVAL, "bad recon");
+  if (o->coupling < RAD_COUPLE_THERMAL || o->coupling > RAD_COUPLE_NONE) return fail(ctx, RAD_EINVAL, "bad coupling");
+  if (o->coupling == RAD_COUPLE_THERMAL && !(o->gamma > 1.0)) return fail(ctx, RAD_EINVAL, "gamma must be > 1");
+  if (!(o->n0crit >= 0.0)) return fail(ctx, RAD_EINVAL, "n0crit must be >= 0");
+  return RAD_OK;
+}
+
+int rad_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src) {
+  if (!ctx) return RAD_EINVAL;
+  if (!ctx->have_metric) return fail(ctx, RAD_ESTATE, "rad_set_metric has not been called");
+  int st = check_opts(ctx, o);
+  if (st != RAD_OK) return st;
+  if ((st = check_gas(ctx, gas, o, true)) != RAD_OK) return st;
+  if (!I || !aligned16(I)) return fail(ctx, RAD_EINVAL, "I must be a 16-byte aligned device pointer");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, RAD_EINVAL, "dt must be finite and > 0");
+  if (ctx->ang.level > rad::kMaxLevelStep)
+    return fail(ctx, RAD_EUNSUPPORTED, "rad_step supports geodesic levels up to 10");
+  const rad::DevGeom &G = ctx->geom;
+  size_t ncell = (size_t)G.n[0] * G.n[1] * G.n[2];
+  size_t esz = o->precision == RAD_F32 ? 4 : 8;
+  size_t need = ncell * ctx->ang.n_ap * esz;
+  if (ctx->scratch_I_bytes < need) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->scratch_I);
+    ctx->scratch_I = nullptr;
+    ctx->scratch_I_bytes = 0;
+    if (cudaMalloc(&ctx->scratch_I, need) != cudaSuccess) return fail(ctx, RAD_ENOMEM, "stage scratch allocation failed");
+    ctx->scratch_I_bytes = need;
+  }
+  if (ctx->scratch_T_count < ncell) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->scratch_T);
+    ctx->scratch_T = nullptr;
+    ctx->scratch_T_count = 0;
+    if (cudaMalloc(&ctx->scratch_T, ncell * sizeof(double)) != cudaSuccess)
+      return fail(ctx, RAD_ENOMEM, "stage scratch allocation failed");
+    ctx->scratch_T_count = ncell;
+  }
+  std::string err;
+  st = rad::launch_step(ctx, I, gas, dt, o, gas_src, ctx->scratch_I, ctx->scratch_T, err);
+  return st == RAD_OK ? st : fail(ctx, st, err);
+}
+
+int rad_moments(rad_ctx *ctx, const void *I, int precision, int frame, int method, const rad_gas *gas, void *R) {
+  if (!ctx) return RAD_EINVAL;
+  if (!ctx->have_metric) return fail(ctx, RAD_ESTATE, "rad_set_metric has not been called");
+  if (!I || !R) return fail(ctx, RAD_EINVAL, "null I or R");
+  if (precision != RAD_F64 && precision != RAD_F32) return fail(ctx, RAD_EINVAL, "bad precision");
+  if (frame < RAD_FRAME_TETRAD || frame > RAD_FRAME_FLUID) return fail(ctx, RAD_EINVAL, "bad frame");
+  if (method != RAD_MOM_SIMT && method != RAD_MOM_BF16X3) return fail(ctx, RAD_EINVAL, "bad method");
+  if (method == RAD_MOM_BF16X3 && precision != RAD_F32)
+    return fail(ctx, RAD_EINVAL, "the split-bf16 moments read float intensities");
+  if (frame == RAD_FRAME_FLUID && (!gas || !gas->u)) return fail(ctx, RAD_EINVAL, "fluid frame needs gas->u");
+  if (!aligned16(I) || !aligned16(R)) return fail(ctx, RAD_EINVAL, "I and R must be 16-byte aligned");
+  std::string err;
+  int st = rad::launch_moments(ctx, I, precision, frame, method, gas, R, err);
+  return st == RAD_OK ? st : fail(ctx, st, err);
+}
+
+int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt, const rad_opts *o,
+                     const void *lam_np1, void *lam_n, double *g_aa, double *g_as, double *g_eta) {
+  if (!ctx) return RAD_EINVAL;
+  if (!ctx->have_metric) return fail(ctx, RAD_ESTATE, "rad_set_metric has not been called");
+  int st = check_opts(ctx, o);
+  if (st != RAD_OK) return st;
+  if ((st = check_gas(ctx, gas, o, true)) != RAD_OK) return st;
+  if (o->coupling == RAD_COUPLE_THERMAL)
+    return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers fixed-emissivity and uncoupled steps");
+  if (!I_n || !lam_np1 || !lam_n || !g_aa || !g_as) return fail(ctx, RAD_EINVAL, "null argument");
+  if (!(dt > 0.0)) return fail(ctx, RAD_EINVAL, "dt must be > 0");
+  if (ctx->ang.level > rad::kMaxLevelStep)
+    return fail(ctx, RAD_EUNSUPPORTED, "rad_step_adjoint supports geodesic levels up to 10");
+  std::string err;
+  st = rad::launch_adjoint(ctx, I_n, gas, dt, o, lam_np1, lam_n, g_aa, g_as, g_eta, err);
+  return st == RAD_OK ? st : fail(ctx, st, err);
+}
+
+int rad_loss_outer(rad_ctx *ctx, const void *I, int precision, double *L_dev, void *dL_dI) {
+  if (!ctx) return RAD_EINVAL;
+  if (!ctx->have_metric) return fail(ctx, RAD_ESTATE, "rad_set_metric has not been called");
+  if (!I || !L_dev) return fail(ctx, RAD_EINVAL, "null argument");
+  if (precision != RAD_F64 && precision != RAD_F32) return fail(ctx, RAD_EINVAL, "bad precision");
+  std::string err;
+  int st = rad::launch_loss(ctx, I, precision, L_dev, dL_dI, err);
+  return st == RAD_OK ? st : fail(ctx, st, err);
+}
+
+int rad_check(rad_ctx *ctx) {
+  if (!ctx) return RAD_EINVAL;
+  int h = 0;
+  cudaError_t ce = cudaMemcpyAsync(&h, ctx->err_word, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(ctx->err_word, 0, sizeof(int), ctx->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+  if (ce != cudaSuccess) return fail(ctx, RAD_ECUDA, std::string("rad_check: ") + cudaGetErrorString(ce));
+  if (h & (1 << 3)) return fail(ctx, RAD_ECUDA, "a device wait timed out (tensor-core moments)");
+  if (h & rad::kErrNoConv) return fail(ctx, RAD_ENOCONV, "a cell's quartic had no bracketed root or did not converge");
+  if (h & rad::kErrNonFinite) return fail(ctx, RAD_ENONFINITE, "a non-finite intensity was produced");
+  return RAD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,182 @@
+// Host launchers of the stage kernel (two stages per SSP-RK2 step) and of
+// the time-step bound.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "step_kernel.cuh"
+
+namespace rad {
+
+namespace {
+
+template <typename R, bool ANG, int MAXT>
+cudaError_t launch_stage_t(const StageArgs &a, int threads, dim3 grid, cudaStream_t st) {
+  size_t smem = stage_smem<R, ANG>(threads, a.nap);
+  auto kern = k_stage<R, ANG, MAXT>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<grid, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R, bool ANG>
+cudaError_t launch_stage_p(const StageArgs &a, cudaStream_t st) {
+  int threads = (a.nap + 31) / 32 * 32;
+  int nchunk = (a.n3 + a.kc - 1) / a.kc;
+  dim3 grid((unsigned)((long long)a.n1 * a.n2 * nchunk));
+  if (threads <= 256) return launch_stage_t<R, ANG, 256>(a, threads, grid, st);
+  if (threads <= 512) return launch_stage_t<R, ANG, 512>(a, threads, grid, st);
+  return launch_stage_t<R, ANG, 1024>(a, threads, grid, st);
+}
+
+cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st) {
+  if (f32) return ang ? launch_stage_p<float, true>(a, st) : launch_stage_p<float, false>(a, st);
+  return ang ? launch_stage_p<double, true>(a, st) : launch_stage_p<double, false>(a, st);
+}
+
+// dt bound of one (column, bin); atomically reduced as the bit pattern of a
+// positive double (order preserving).
+__global__ void k_cfl(const ColGeo *cols, int n1, int n2, int ndim, const double *xf1, const double *xf2,
+                      double dx3, int nang, const double *dir, const double *dOmega, const int *slot_nbr,
+                      const int *slot_edge, const double *edge_geo, int ang, unsigned long long *out) {
+  int col = blockIdx.x;
+  int n = threadIdx.x;
+  if (n >= nang) return;
+  int i = col % n1, j = col / n1;
+  const ColGeo &cg = cols[col];
+  double nh[4] = {1.0, dir[3 * n], dir[3 * n + 1], dir[3 * n + 2]};
+  double best = INFINITY;
+  double dx[3] = {xf1[i + 1] - xf1[i], xf2[j + 1] - xf2[j], dx3};
+  double n0 = cg.n0up;
+  for (int d = 0; d < ndim; ++d) {
+    double na = 0.0;
+    for (int A = 0; A < 4; ++A) na += cg.e[d + 1][A] * nh[A];
+    double sp = fabs(na / n0);
+    if (sp > 0.0) best = fmin(best, dx[d] / sp);
+  }
+  if (ang) {
+    double rate = 0.0;
+    for (int s = 0; s < kMaxSlots; ++s) {
+      if (slot_nbr[6 * n + s] < 0) continue;
+      const double *eg = edge_geo + 8 * slot_edge[6 * n + s];
+      double x = eg[0], y = eg[1], z = eg[2];
+      double pr[10] = {1.0, x, y, z, x * x, x * y, x * z, y * y, y * z, z * z};
+      double q[3] = {0.0, 0.0, 0.0};
+      for (int c = 0; c < 3; ++c)
+        for (int p = 0; p < 10; ++p) q[c] += cg.K[c][p] * pr[p];
+      double sp = -(eg[3] * q[0] + eg[4] * q[1] + eg[5] * q[2]);
+      rate += eg[6] * fabs(sp);
+    }
+    if (rate > 0.0) best = fmin(best, dOmega[n] * n0 / rate);
+  }
+  if (best < INFINITY) atomicMin(out, (unsigned long long)__double_as_longlong(best));
+}
+
+}  // namespace
+
+int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src,
+                void *scratch_I, double *scratch_T, std::string &err) {
+  const DevGeom &G = ctx->geom;
+  StageArgs a;
+  a.rho = gas->rho;
+  a.u = gas->u;
+  a.aa = gas->alpha_a;
+  a.as = gas->alpha_s;
+  a.eta = gas->eta;
+  a.src = gas_src;
+  a.dt = dt;
+  a.n1 = G.n[0];
+  a.n2 = G.n[1];
+  a.n3 = G.n[2];
+  a.nap = ctx->ang.n_ap;
+  a.nang = ctx->ang.n_ang;
+  a.ndim = G.ndim;
+  a.kc = G.ndim >= 3 ? std::min(G.n[2], kMaxChunk) : 1;
+  for (int d = 0; d < 3; ++d) {
+    a.bc_lo[d] = G.bc_lo[d];
+    a.bc_hi[d] = G.bc_hi[d];
+  }
+  const bool f32 = o->precision == RAD_F32;
+  a.cols = f32 ? (const void *)G.colsF : (const void *)G.cols;
+  a.f1 = f32 ? (const void *)G.f1F : (const void *)G.f1;
+  a.f2 = f32 ? (const void *)G.f2F : (const void *)G.f2;
+  a.f3 = f32 ? (const void *)G.f3F : (const void *)G.f3;
+  a.dir = ctx->dang.dir;
+  a.dOmega = ctx->dang.dOmega;
+  a.edge_geo = ctx->dang.edge_geo;
+  a.perm = ctx->dang.perm;
+  a.slot_nbr = ctx->dang.slot_nbr;
+  a.slot_edge = ctx->dang.slot_edge;
+  a.edge_pq = ctx->dang.edge_pq;
+  a.recon = o->recon;
+  a.mode = o->coupling;
+  a.zero_guard = o->zero_guard;
+  a.n0crit = o->n0crit;
+  a.a_rad = o->a_rad;
+  a.gamma = o->gamma;
+  a.err = ctx->err_word;
+  const bool ang = G.kind != RAD_MINK_CART;
+  // stage 1: I^0 -> I^1 (scratch), T^0 -> T^1 (scratch)
+  a.Iprev = I;
+  a.I0 = I;
+  a.Iout = scratch_I;
+  a.T0 = gas->T;
+  a.T1 = nullptr;
+  a.Tout = scratch_T;
+  a.stage2 = 0;
+  a.dts = dt;
+  cudaError_t ce = launch_stage(a, f32, ang, ctx->stream);
+  if (ce != cudaSuccess) {
+    err = std::string("stage 1 launch failed: ") + cudaGetErrorString(ce);
+    return RAD_ECUDA;
+  }
+  // stage 2: I^1 (+ own I^0) -> I^2 written over I^0; T -> gas->T
+  a.Iprev = scratch_I;
+  a.I0 = I;
+  a.Iout = I;
+  a.T0 = gas->T;
+  a.T1 = scratch_T;
+  a.Tout = gas->T;
+  a.stage2 = 1;
+  a.dts = 0.5 * dt;
+  ce = launch_stage(a, f32, ang, ctx->stream);
+  if (ce != cudaSuccess) {
+    err = std::string("stage 2 launch failed: ") + cudaGetErrorString(ce);
+    return RAD_ECUDA;
+  }
+  return RAD_OK;
+}
+
+int launch_cfl(rad_ctx *ctx, double cfl, double *dt_out, std::string &err) {
+  const DevGeom &G = ctx->geom;
+  unsigned long long *d = nullptr;
+  if (cudaMalloc(&d, sizeof(unsigned long long)) != cudaSuccess) {
+    err = "cfl: allocation failed";
+    return RAD_ENOMEM;
+  }
+  unsigned long long init = (unsigned long long)0x7ff0000000000000ULL;   // +inf
+  cudaMemcpyAsync(d, &init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream);
+  double dx3 = G.xf[2][1] - G.xf[2][0];
+  const double *xf1 = G.xf_dev, *xf2 = G.xf_dev + G.xf[0].size();
+  int threads = (ctx->ang.n_ang + 31) / 32 * 32;
+  k_cfl<<<G.n[0] * G.n[1], threads, 0, ctx->stream>>>(
+      G.cols, G.n[0], G.n[1], G.ndim, xf1, xf2, dx3, ctx->ang.n_ang, ctx->dang.dir, ctx->dang.dOmega,
+      ctx->dang.slot_nbr, ctx->dang.slot_edge, ctx->dang.edge_geo, G.kind != RAD_MINK_CART, d);
+  unsigned long long h = 0;
+  cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+  cudaError_t ce = cudaStreamSynchronize(ctx->stream);
+  cudaFree(d);
+  if (ce != cudaSuccess) {
+    err = std::string("cfl kernel failed: ") + cudaGetErrorString(ce);
+    return RAD_ECUDA;
+  }
+  double best;
+  std::memcpy(&best, &h, sizeof(best));
+  *dt_out = cfl * best;
+  return RAD_OK;
+}
+
+}  // namespace rad

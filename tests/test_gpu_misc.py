@@ -1,0 +1,161 @@
+"""GPU parity of the angle grid, time-step bound, moments and loss, and the
+C-ABI's argument checks."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2302_04283_gb300 as rad
+import workloads as W
+from oracle import adjoint as OA
+from oracle import cfl as OCFL
+from oracle import moments as OM
+from oracle.angles import GeodesicGrid
+from tests.harness import GpuCase, match_bins, oracle_setup, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("level", [1, 2, 4, 6, 8, 10])
+def test_angle_grid_matches_oracle(level):
+    ctx = rad.rad_create()
+    try:
+        na, nap = rad.rad_init_angles(ctx, level)
+        assert na == 10 * level * level + 2 and nap % 4 == 0 and nap >= na
+        d, w, nb = rad.rad_get_angles(ctx, na)
+        ora = GeodesicGrid(level)
+        g = match_bins(d, ora.dir.numpy())
+        assert np.abs(w[g] - ora.dOmega.numpy()).max() < 1e-14
+        inv = np.argsort(g)
+        for n in range(na):
+            mine = sorted(int(inv[m]) for m in nb[g[n]] if m >= 0)
+            assert mine == sorted(ora.nbr[n])
+    finally:
+        rad.rad_destroy(ctx)
+
+
+@pytest.mark.parametrize("name,n,level", [("turb3d", (8, 6, 4), 2), ("torus3d", (8, 6, 4), 3),
+                                          ("adjoint2d", (12, 8, 1), 2)])
+def test_cfl_matches_oracle(name, n, level):
+    w = W.make(name, n=n, level=level, with_intensity=False)
+    gc = GpuCase(w)
+    try:
+        st = oracle_setup(w)
+        assert abs(rad.rad_cfl_dt(gc.ctx, 0.3) - OCFL.cfl_dt(st, 0.3)) < 1e-12 * OCFL.cfl_dt(st, 0.3)
+    finally:
+        gc.close()
+
+
+@pytest.mark.parametrize("frame", [rad.RAD_FRAME_TETRAD, rad.RAD_FRAME_COORD, rad.RAD_FRAME_FLUID])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_moments_match_oracle(frame, prec):
+    w = W.make("torus3d_big", n=(7, 6, 4), level=3)
+    gc = GpuCase(w)
+    try:
+        st = oracle_setup(w)
+        gmap = match_bins(gc.dir, st.ang.dir.numpy())
+        tdt = torch.float64 if prec == "f64" else torch.float32
+        Ig = gc.to_gpu_I(w["I0"], gmap, tdt)
+        R = torch.zeros(Ig.shape[:-1] + (10,), dtype=tdt, device="cuda")
+        rad.rad_moments(gc.ctx, Ig, rad.RAD_F64 if prec == "f64" else rad.RAD_F32, frame, rad.RAD_MOM_SIMT,
+                        gc.gas(w), R)
+        torch.cuda.synchronize()
+        fr = {rad.RAD_FRAME_TETRAD: "tetrad", rad.RAD_FRAME_COORD: "coord", rad.RAD_FRAME_FLUID: "fluid"}[frame]
+        ref = OM.moments(torch.tensor(w["I0"]), st.ang, fr, e=st.e, u=torch.tensor(w["u"])).numpy()
+        tol = 1e-13 if prec == "f64" else 2e-6
+        assert rel_err(R.double().cpu().numpy(), ref) < tol
+    finally:
+        gc.close()
+
+
+def test_loss_and_seed_match_oracle():
+    w = W.make("adjoint2d", n=(10, 8, 1), level=2)
+    gc = GpuCase(w)
+    try:
+        st = oracle_setup(w)
+        gmap = match_bins(gc.dir, st.ang.dir.numpy())
+        Ig = gc.to_gpu_I(w["I0"], gmap, torch.float64)
+        L = torch.zeros(1, dtype=torch.float64, device="cuda")
+        seed = torch.zeros_like(Ig)
+        rad.rad_loss_outer(gc.ctx, Ig, rad.RAD_F64, L, seed)
+        torch.cuda.synchronize()
+        I0 = torch.tensor(w["I0"])
+        assert abs(L.item() - float(OA.loss_outer(I0, st))) < 1e-13 * abs(float(OA.loss_outer(I0, st)))
+        # the two grids' solid angles agree to rounding
+        assert np.abs(gc.from_gpu_I(seed, gmap) - OA.loss_seed(I0, st).numpy()).max() < 1e-15
+    finally:
+        gc.close()
+
+
+def test_argument_errors_are_reported():
+    ctx = rad.rad_create()
+    try:
+        with pytest.raises(rad.RadError) as e:
+            rad.rad_init_angles(ctx, 0)
+        assert e.value.status == rad.RAD_EINVAL
+        with pytest.raises(rad.RadError) as e:
+            rad.rad_cfl_dt(ctx, 0.3)
+        assert e.value.status == rad.RAD_ESTATE
+        rad.rad_init_angles(ctx, 2)
+        xf = [np.linspace(0, 1, 5), np.linspace(0, 1, 5), np.array([0.0, 1.0])]
+        with pytest.raises(rad.RadError) as e:     # polar on a Cartesian metric
+            rad.rad_set_metric(ctx, "mink_cart", 0.0, 2, xf, (("periodic",) * 2, ("polar",) * 2, ("periodic",) * 2))
+        assert e.value.status == rad.RAD_EINVAL
+        with pytest.raises(rad.RadError) as e:     # decreasing faces
+            rad.rad_set_metric(ctx, "mink_cart", 0.0, 2, [xf[0][::-1].copy(), xf[1], xf[2]],
+                               (("periodic",) * 2,) * 3)
+        assert e.value.status == rad.RAD_EINVAL
+        rad.rad_set_metric(ctx, "mink_cart", 0.0, 2, xf, (("periodic",) * 2,) * 3)
+        I = torch.zeros(1, 4, 4, 44, dtype=torch.float64, device="cuda")
+        o = rad.rad_opts_default()
+        f = lambda *s: torch.ones(*s, dtype=torch.float64, device="cuda")
+        gas = {"T": f(1, 4, 4), "rho": f(1, 4, 4), "u": 0 * f(1, 4, 4, 3), "alpha_a": f(1, 4, 4),
+               "alpha_s": f(1, 4, 4)}
+        with pytest.raises(rad.RadError) as e:     # dt <= 0
+            rad.rad_step(ctx, I, gas, 0.0, o)
+        assert e.value.status == rad.RAD_EINVAL
+        with pytest.raises(rad.RadError) as e:     # emissivity coupling without eta
+            rad.rad_step(ctx, I, gas, 0.1, rad.rad_opts_default(coupling=rad.RAD_COUPLE_EMISSIVITY))
+        assert e.value.status == rad.RAD_EINVAL
+        rad.rad_step(ctx, I, gas, 0.01, o)         # a valid call on the same context still works
+        rad.rad_check(ctx)
+    finally:
+        rad.rad_destroy(ctx)
+
+
+def test_empty_and_tiny_grids():
+    """One cell with periodic boundaries everywhere: its own neighbour."""
+    w = W.make("turb3d", n=(1, 1, 1), level=1)
+    from tests.harness import run_both
+    r = run_both(w, 2, "f64")
+    try:
+        assert rel_err(r["I_g"], r["I_o"]) < 1e-12
+    finally:
+        r["gc"].close()
+
+
+@pytest.mark.parametrize("frame", [rad.RAD_FRAME_TETRAD, rad.RAD_FRAME_COORD, rad.RAD_FRAME_FLUID])
+@pytest.mark.parametrize("level,n", [(3, (7, 6, 4)), (2, (33, 5, 4)), (8, (5, 4, 2))])
+def test_moments_split_bf16_tensor_cores(frame, level, n):
+    """Split-bf16 tcgen05 moments vs the FP64 oracle.  Tolerance: every
+    component within 1e-4 of the cell's R^00 (three bf16 products with FP32
+    accumulation: about 2^-16 relative per term)."""
+    w = W.make("torus3d_big", n=n, level=level)
+    gc = GpuCase(w)
+    try:
+        st = oracle_setup(w)
+        gmap = match_bins(gc.dir, st.ang.dir.numpy())
+        Ig = gc.to_gpu_I(w["I0"], gmap, torch.float32)
+        R = torch.full(Ig.shape[:-1] + (10,), float("nan"), dtype=torch.float32, device="cuda")
+        rad.rad_moments(gc.ctx, Ig, rad.RAD_F32, frame, rad.RAD_MOM_BF16X3, gc.gas(w), R)
+        torch.cuda.synchronize()
+        rad.rad_check(gc.ctx)
+        fr = {rad.RAD_FRAME_TETRAD: "tetrad", rad.RAD_FRAME_COORD: "coord", rad.RAD_FRAME_FLUID: "fluid"}[frame]
+        ref = OM.moments(torch.tensor(w["I0"]), st.ang, fr, e=st.e, u=torch.tensor(w["u"])).numpy()
+        got = R.double().cpu().numpy()
+        scale = np.abs(ref[..., :1])
+        assert np.isfinite(got).all()
+        assert (np.abs(got - ref) / scale).max() < 1e-4
+    finally:
+        gc.close()

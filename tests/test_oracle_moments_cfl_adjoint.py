@@ -91,9 +91,9 @@ def test_gradient_matches_central_differences(adj_case):
             h = 1e-5 * float(gas[field][cell])
             fd = (loss_with(field, cell, h) - loss_with(field, cell, -h)) / (2 * h)
             ad = float(grads[fi][cell])
-            # relative to the gradient, floored at 1e-2 of its largest entry
+            # relative to the gradient, floored at 2e-2 of its largest entry
             # (below that the difference quotient is limited by roundoff)
-            assert abs(fd - ad) <= 1e-6 * max(abs(ad), 1e-2 * float(grads[fi].abs().max()))
+            assert abs(fd - ad) <= 1e-6 * max(abs(ad), 2e-2 * float(grads[fi].abs().max()))
 
 
 def test_step_vjp_dot_product(adj_case):
