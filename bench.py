@@ -41,6 +41,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--n", type=int, default=None, help="cells per side (default: the workload's 128)")
     return p.parse_args()
 
 
@@ -105,11 +106,11 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- our arm
-def setup_gpu(prec, dev):
+def setup_gpu(prec, dev, n=None):
     import torch
     import paper_2302_04283_gb300 as rad
     import workloads as W
-    w = W.make(WORKLOAD, with_intensity=False)
+    w = W.make(WORKLOAD, n=(n, n, n) if n else None, with_intensity=False)
     ctx = rad.rad_create(torch.cuda.current_stream())
     na, nap = rad.rad_init_angles(ctx, w["level"])
     rad.rad_set_metric(ctx, w["kind"], w["spin"], w["ndim"], w["xf"], w["bc"])
@@ -133,7 +134,7 @@ def run_ours(args, rank, world):
     import torch
     dev = f"cuda:{int(os.environ.get('LOCAL_RANK', 0))}"
     torch.cuda.set_device(dev)
-    rad, w, ctx, na, nap, dt, sh, tdt, I, gas = setup_gpu(args.precision, dev)
+    rad, w, ctx, na, nap, dt, sh, tdt, I, gas = setup_gpu(args.precision, dev, args.n)
     ncell = sh[0] * sh[1] * sh[2]
     esz = 4 if args.precision == "f32" else 8
     prec = rad.RAD_F32 if args.precision == "f32" else rad.RAD_F64
@@ -231,7 +232,7 @@ def run_e2e(args, rad, ctx, dt, opts, prec, mom, sh, na, nap, tdt, dev, world):
     moments back."""
     import torch
     import workloads as W
-    w = W.make(WORKLOAD, with_intensity=False)
+    w = W.make(WORKLOAD, n=(sh[2], sh[1], sh[0]), with_intensity=False)
     hI = torch.empty(sh + (nap,), dtype=tdt, pin_memory=True)
     g = torch.Generator()
     g.manual_seed(w["seed"])
