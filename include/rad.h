@@ -159,6 +159,25 @@ int rad_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt,
              const rad_opts *opts, double *gas_src);
 
 /*
+ * rad_step without any device allocation (the paper has no counterpart; this
+ * is a service of this library).  For callers that may not allocate device
+ * memory once running: a host framework that owns all device memory through
+ * its own pool, or a loop that cannot take the implicit synchronisation of
+ * cudaMalloc / cudaFree.  Same arguments, arithmetic and results as
+ * rad_step, but the stage scratch (one intensity array and one temperature
+ * array) lives in a 32 MiB static device array that every GPU loading this
+ * library holds until the process exits.  Grids needing more
+ * (n_cells * n_ang_padded * element size, rounded up to 256 bytes, plus
+ * 8 bytes per cell) are refused with RAD_EINVAL.  Calls share that array:
+ * calls that overlap on the GPU (other streams or contexts on the same
+ * device) race.  The first call on a device, with that device current, looks
+ * up the array's device address; make that first call before any stream
+ * capture.  Calls no cudaMalloc or cudaFree.
+ */
+int rad_step_noalloc(rad_ctx *ctx, void *I, const rad_gas *gas, double dt,
+                     const rad_opts *opts, double *gas_src);
+
+/*
  * Moments R^{AB} = sum_n I_n n^A n^B dOmega_n of every cell, written as 10
  * components [cell][10] in the order 00 01 02 03 11 12 13 22 23 33.
  * precision: element type of I (and of R for RAD_MOM_BF16X3, which writes

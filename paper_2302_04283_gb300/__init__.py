@@ -82,6 +82,7 @@ def lib():
         "rad_set_metric": ([_vp, P(rad_metric), P(rad_grid)], ctypes.c_int),
         "rad_cfl_dt": ([_vp, ctypes.c_double, P(ctypes.c_double)], ctypes.c_int),
         "rad_step": ([_vp, _vp, P(rad_gas), ctypes.c_double, P(rad_opts), _vp], ctypes.c_int),
+        "rad_step_noalloc": ([_vp, _vp, P(rad_gas), ctypes.c_double, P(rad_opts), _vp], ctypes.c_int),
         "rad_moments": ([_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(rad_gas), _vp], ctypes.c_int),
         "rad_step_adjoint": ([_vp, _vp, P(rad_gas), ctypes.c_double, P(rad_opts), _vp, _vp, _vp, _vp, _vp],
                              ctypes.c_int),
@@ -179,6 +180,14 @@ def _gas(gas):
 def rad_step(ctx, I, gas, dt, opts, gas_src=None):
     g = _gas(gas)
     _check(ctx, lib().rad_step(ctx, _ptr(I), ctypes.byref(g), float(dt), ctypes.byref(opts), _ptr(gas_src)))
+
+
+def rad_step_noalloc(ctx, I, gas, dt, opts, gas_src=None):
+    """rad_step with its stage scratch in the library's static device array
+    (no device allocation; see include/rad.h for the size limit)."""
+    g = _gas(gas)
+    _check(ctx, lib().rad_step_noalloc(ctx, _ptr(I), ctypes.byref(g), float(dt), ctypes.byref(opts),
+                                       _ptr(gas_src)))
 
 
 def rad_moments(ctx, I, precision, frame, method, gas, R):
