@@ -64,6 +64,7 @@ void rad_destroy(rad_ctx *ctx) {
   cudaFree(ctx->scratch_T);
   cudaFree(ctx->adj_buf);
   cudaFree(ctx->wt_dev);
+  cudaFree(ctx->loss_buf);
   delete ctx;
 }
 

@@ -115,6 +115,9 @@ struct rad_ctx {
   // split-bf16 moment weights (W^T hi / lo in the tensor-core operand layout)
   void *wt_dev = nullptr;
   int wt_kp = 0, wt_level = 0;
+  // per-row partials of the outgoing-flux loss
+  double *loss_buf = nullptr;
+  int loss_rows = 0;
 };
 
 namespace rad {

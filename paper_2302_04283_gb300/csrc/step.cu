@@ -32,10 +32,6 @@ cudaError_t launch_stage_p(const StageArgs &a, cudaStream_t st) {
   return launch_stage_t<R, ANG, 1024>(a, threads, grid, st);
 }
 
-cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st) {
-  if (f32) return ang ? launch_stage_p<float, true>(a, st) : launch_stage_p<float, false>(a, st);
-  return ang ? launch_stage_p<double, true>(a, st) : launch_stage_p<double, false>(a, st);
-}
 
 // dt bound of one (column, bin); atomically reduced as the bit pattern of a
 // positive double (order preserving).
@@ -77,10 +73,15 @@ __global__ void k_cfl(const ColGeo *cols, int n1, int n2, int ndim, const double
 
 }  // namespace
 
-int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src,
-                void *scratch_I, double *scratch_T, std::string &err) {
+cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st) {
+  if (f32) return ang ? launch_stage_p<float, true>(a, st) : launch_stage_p<float, false>(a, st);
+  return ang ? launch_stage_p<double, true>(a, st) : launch_stage_p<double, false>(a, st);
+}
+
+StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src) {
   const DevGeom &G = ctx->geom;
   StageArgs a;
+  a.Istar = nullptr;
   a.rho = gas->rho;
   a.u = gas->u;
   a.aa = gas->alpha_a;
@@ -88,6 +89,8 @@ int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_
   a.eta = gas->eta;
   a.src = gas_src;
   a.dt = dt;
+  a.dts = dt;
+  a.stage2 = 0;
   a.n1 = G.n[0];
   a.n2 = G.n[1];
   a.n3 = G.n[2];
@@ -118,7 +121,14 @@ int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_
   a.a_rad = o->a_rad;
   a.gamma = o->gamma;
   a.err = ctx->err_word;
-  const bool ang = G.kind != RAD_MINK_CART;
+  return a;
+}
+
+int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src,
+                void *scratch_I, double *scratch_T, std::string &err) {
+  StageArgs a = make_stage_args(ctx, gas, dt, o, gas_src);
+  const bool f32 = o->precision == RAD_F32;
+  const bool ang = ctx->geom.kind != RAD_MINK_CART;
   // stage 1: I^0 -> I^1 (scratch), T^0 -> T^1 (scratch)
   a.Iprev = I;
   a.I0 = I;

@@ -41,6 +41,7 @@ struct StageArgs {
   const void *Iprev;      // I^{s-1}: neighbours and own bin (read-only)
   const void *I0;         // I^0 (own bin, stage 2)
   void *Iout;
+  void *Istar;            // optional copy of the pre-coupling primitive I* (adjoint recompute)
   const double *T0, *T1;  // T^0, and T^1 for stage 2
   double *Tout;
   const double *rho, *u, *aa, *as, *eta;
@@ -57,6 +58,9 @@ struct StageArgs {
   double n0crit, a_rad, gamma;
   int *err;
 };
+
+StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src);
+cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st);
 
 template <typename R> struct GeoTypes;
 template <> struct GeoTypes<double> { using Col = ColGeo; using Face = FaceGeo; };
@@ -383,7 +387,10 @@ __global__ void __launch_bounds__(MAXT) k_stage(StageArgs a) {
       Us = Uprev + dtR * L;
     }
     const R Is = (guard || !act) ? R(0) : Us * inv_f;
-    if (act) Io[(long long)k * strideK + own] = Is;
+    if (act) {
+      Io[(long long)k * strideK + own] = Is;
+      if (a.Istar) ((R *)a.Istar)[(long long)k * strideK + own] = Is;
+    }
     if (couple) {
       const R ux = sgas[4 * c], uy = sgas[4 * c + 1], uz = sgas[4 * c + 2], aE = sgas[4 * c + 3];
       const R nb = su0[c] - (ux * nh0 + uy * nh1 + uz * nh2);
