@@ -30,9 +30,11 @@
  *     Newton iteration) set a sticky error word in device memory instead of
  *     trapping; rad_check reads and clears it.
  *   - Intensity layout: I[k][j][i][n] for k < n[2], j < n[1], i < n[0],
- *     n < n_ang_padded (angle fastest).  Bins n >= n_ang are padding: never
- *     read as data and never written.  Element type is double (RAD_F64) or
- *     float (RAD_F32).  There are no ghost cells in the array: boundary
+ *     n < n_ang_padded (angle fastest).  Bins n >= n_ang are padding: their
+ *     values are never used, and rad_step writes them as 0.  Element type is
+ *     double (RAD_F64) or
+ *     float (RAD_F32).  A block may hold at most 2^32 elements.  There are no
+ *     ghost cells in the array: boundary
  *     conditions are applied by index mapping when neighbours are read.
  *   - Coordinates are (x1, x2, x3); for spherical metrics (r, theta, phi).
  */

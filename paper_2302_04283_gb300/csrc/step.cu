@@ -10,26 +10,30 @@ namespace rad {
 
 namespace {
 
-template <typename R, bool ANG, int MAXT>
+template <typename R, bool ANG, bool PLM, bool ST2>
 cudaError_t launch_stage_t(const StageArgs &a, int threads, dim3 grid, cudaStream_t st) {
-  size_t smem = stage_smem<R, ANG>(threads, a.nap);
-  auto kern = k_stage<R, ANG, MAXT>;
+  size_t smem = stage_smem<R, ANG>(threads, a.nap, a.kc);
+  auto kern = k_stage<R, ANG, PLM, ST2>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<grid, threads, smem, st>>>(a);
+  // the kernel keeps its working set in shared memory: prefer the largest carve-out
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  kern<<<grid, threads + 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <typename R, bool ANG>
 cudaError_t launch_stage_p(const StageArgs &a, cudaStream_t st) {
-  int threads = (a.nap + 31) / 32 * 32;
+  int threads = (a.nap / 2 + 31) / 32 * 32;     // two bins per consumer thread
   int nchunk = (a.n3 + a.kc - 1) / a.kc;
   dim3 grid((unsigned)((long long)a.n1 * a.n2 * nchunk));
-  if (threads <= 256) return launch_stage_t<R, ANG, 256>(a, threads, grid, st);
-  if (threads <= 512) return launch_stage_t<R, ANG, 512>(a, threads, grid, st);
-  return launch_stage_t<R, ANG, 1024>(a, threads, grid, st);
+  const bool plm = a.recon == RAD_RECON_PLM;
+  if (plm) return a.stage2 ? launch_stage_t<R, ANG, true, true>(a, threads, grid, st)
+                           : launch_stage_t<R, ANG, true, false>(a, threads, grid, st);
+  return a.stage2 ? launch_stage_t<R, ANG, false, true>(a, threads, grid, st)
+                  : launch_stage_t<R, ANG, false, false>(a, threads, grid, st);
 }
 
 
@@ -97,7 +101,12 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
   a.nap = ctx->ang.n_ap;
   a.nang = ctx->ang.n_ang;
   a.ndim = G.ndim;
-  a.kc = G.ndim >= 3 ? std::min(G.n[2], kMaxChunk) : 1;
+  // cells per CTA along x3: up to kMaxChunk, fewer when the chunk's I* does
+  // not fit the shared-memory budget
+  const size_t esz = o->precision == RAD_F32 ? 4 : 8;
+  const long long rows_fit = (long long)(200 * 1024) / ((long long)ctx->ang.n_ap * esz) - kStages * kRows;
+  const int kc_mem = (int)std::max<long long>(1, rows_fit);
+  a.kc = G.ndim >= 3 ? std::min(std::min(G.n[2], kMaxChunk), kc_mem) : 1;
   for (int d = 0; d < 3; ++d) {
     a.bc_lo[d] = G.bc_lo[d];
     a.bc_hi[d] = G.bc_hi[d];
@@ -129,6 +138,18 @@ int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_
   StageArgs a = make_stage_args(ctx, gas, dt, o, gas_src);
   const bool f32 = o->precision == RAD_F32;
   const bool ang = ctx->geom.kind != RAD_MINK_CART;
+  if ((size_t)a.n1 * a.n2 * a.n3 * a.nap >= ((size_t)1 << 32)) {
+    err = "rad_step: more than 2^32 intensity elements in one block";
+    return RAD_EUNSUPPORTED;
+  }
+  {
+    const int threads = (a.nap / 2 + 31) / 32 * 32;
+    const size_t smem = f32 ? stage_smem<float, false>(threads, a.nap, a.kc) : stage_smem<double, false>(threads, a.nap, a.kc);
+    if (smem > (size_t)227 * 1024) {
+      err = "rad_step: the stencil pipeline of this many bins does not fit shared memory in this precision";
+      return RAD_EUNSUPPORTED;
+    }
+  }
   // stage 1: I^0 -> I^1 (scratch), T^0 -> T^1 (scratch)
   a.Iprev = I;
   a.I0 = I;

@@ -5,11 +5,13 @@
 // n0crit guard (Sec. 2.4).
 //
 // Work decomposition: one CTA per (i, j) column and chunk of at most
-// kMaxChunk cells along x3; one thread per angle bin.  The metrics are
+// kMaxChunk cells along x3; each thread owns two adjacent angle bins (vector
+// loads, packed FP32x2 arithmetic on sm_103a).  The metrics are
 // x3-independent, so every geometric prefactor of a bin is built once per
 // CTA (in the working precision, from the per-column tables) and kept in
-// registers while the thread walks the chunk along x3 with the x3 stencil in
-// a sliding register window.  x1 / x2 neighbours are coalesced row loads.
+// registers while the thread walks the chunk along x3 with the x3 stencil
+// and its limiter slopes in a sliding register window.  x1 / x2 neighbours
+// are coalesced row loads.
 // Boundary conditions are applied by index mapping (no ghost cells):
 // periodic wrap, outflow clamp, and the polar map (theta -> -theta,
 // phi -> phi + pi, bin n -> perm[n]).
@@ -177,84 +179,200 @@ __device__ __forceinline__ int wrap_idx(int x, int n, int bc_lo, int bc_hi, int 
   return x;
 }
 
-// Shared-memory footprint (bytes) of k_stage for a block of `threads`.
-template <typename R, bool ANG>
-__host__ __device__ constexpr size_t stage_smem(int threads, int nap) {
-  return (size_t)kMaxChunk * 4 * sizeof(R)                          // gas: ux uy uz alphaE
-         + (size_t)kMaxChunk * sizeof(R)                            // u^0hat
-         + (size_t)kMaxChunk * (threads / 32) * kNRedC * sizeof(R)  // per-warp partial sums
-         + (size_t)kMaxChunk * kNRedC * sizeof(R)                   // cell sums
-         + (size_t)kMaxChunk * sizeof(R)                            // S per cell
-         + (ANG ? (size_t)2 * nap * sizeof(R) : 0);                 // own-cell rows
+// ---------------------------------------------------------------- pairs
+// Two bins per thread.  For float the arithmetic uses the packed FP32x2
+// instructions of sm_100+ (one instruction for both bins); for double it is
+// two scalar operations.
+template <typename R> struct P2;
+template <> struct P2<float> {
+  using V = float2;
+  static __device__ __forceinline__ V mk(float a, float b) { return make_float2(a, b); }
+  static __device__ __forceinline__ V add(V a, V b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ V sub(V a, V b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+  static __device__ __forceinline__ V mul(V a, V b) { return __fmul2_rn(a, b); }
+  static __device__ __forceinline__ V fma(V a, V b, V c) { return __ffma2_rn(a, b, c); }
+  // approximate reciprocal (MUFU, ~1 ulp): the FP32 path's stated tolerance allows it
+  static __device__ __forceinline__ V rcp(V a) { return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y)); }
+};
+template <> struct P2<double> {
+  using V = double2;
+  static __device__ __forceinline__ V mk(double a, double b) { return make_double2(a, b); }
+  static __device__ __forceinline__ V add(V a, V b) { return make_double2(a.x + b.x, a.y + b.y); }
+  static __device__ __forceinline__ V sub(V a, V b) { return make_double2(a.x - b.x, a.y - b.y); }
+  static __device__ __forceinline__ V mul(V a, V b) { return make_double2(a.x * b.x, a.y * b.y); }
+  static __device__ __forceinline__ V fma(V a, V b, V c) { return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
+  static __device__ __forceinline__ V rcp(V a) { return make_double2(1.0 / a.x, 1.0 / a.y); }
+};
+
+// van Leer half-slopes of a pair: q = dl dr / (dl + dr) if dl dr > 0, else 0.
+template <typename R>
+__device__ __forceinline__ typename P2<R>::V vl2(typename P2<R>::V x, typename P2<R>::V y, typename P2<R>::V z) {
+  using P = P2<R>;
+  auto dl = P::sub(y, x), dr = P::sub(z, y);
+  auto prod = P::mul(dl, dr);
+  auto s = P::add(dl, dr);
+  // both quotients are formed unconditionally and the select discards the
+  // ones of non-positive products (including 0/0), so no branch is taken
+  const R qx = fdiv(prod.x, s.x), qy = fdiv(prod.y, s.y);
+  return P::mk(prod.x > R(0) ? qx : R(0), prod.y > R(0) ? qy : R(0));
 }
 
-template <typename R, bool ANG, int MAXT>
-__global__ void __launch_bounds__(MAXT) k_stage(StageArgs a) {
+template <typename R>
+__device__ __forceinline__ typename P2<R>::V sel2(bool cx, bool cy, typename P2<R>::V a, typename P2<R>::V b) {
+  return P2<R>::mk(cx ? a.x : b.x, cy ? a.y : b.y);
+}
+
+// Upwind face values of the lower (m1|c) and upper (c|p1) faces from the
+// three half-slopes q(m2,m1,c), q(m1,c,p1), q(c,p1,p2) of the pair.
+template <typename R>
+__device__ __forceinline__ typename P2<R>::V face_div(unsigned um, unsigned up, typename P2<R>::V cm,
+                                                    typename P2<R>::V cp, typename P2<R>::V m1,
+                                                    typename P2<R>::V c, typename P2<R>::V p1,
+                                                    typename P2<R>::V qm, typename P2<R>::V qc,
+                                                    typename P2<R>::V qp) {
+  using P = P2<R>;
+  const bool umx = um & 1, umy = um & 2, upx = up & 1, upy = up & 2;
+  auto lo = P::add(sel2<R>(umx, umy, c, m1), sel2<R>(umx, umy, P::mk(-qc.x, -qc.y), qm));
+  auto hi = P::add(sel2<R>(upx, upy, p1, c), sel2<R>(upx, upy, P::mk(-qp.x, -qp.y), qc));
+  return P::sub(P::mul(cp, hi), P::mul(cm, lo));
+}
+
+// ---------------------------------------------------------------- TMA
+// One-dimensional bulk copies (the TMA engine) global -> shared, completing
+// on an mbarrier with a transaction count.  Rows are n_ap elements, a
+// multiple of 16 bytes, and start on 16-byte boundaries.
+constexpr int kStages = 4;          // ring depth of the stencil pipeline
+constexpr int kStageMaxThreads = 512 + 32;   // consumers (two bins each) + one producer warp
+constexpr int kRows = 11;           // rows per stage (see k_stage)
+constexpr long long kSpinLimit = 1ll << 28;
+
+__device__ __forceinline__ uint32_t s_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_addr(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(s_addr(dst)),
+      "l"(src), "r"(bytes), "r"(s_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_parity(uint64_t *bar, uint32_t parity) {
+  const uint32_t a = s_addr(bar);
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Shared-memory footprint (bytes) of k_stage.
+template <typename R, bool ANG>
+__host__ __device__ constexpr size_t stage_smem(int threads, int nap, int kc) {
+  return (size_t)kStages * kRows * nap * sizeof(R)              // staged stencil rows
+         + (size_t)kc * nap * sizeof(R)                         // I* of the chunk
+         + (size_t)kc * 5 * sizeof(R)                           // gas ux uy uz alphaE u0
+         + (size_t)kc * (threads / 32) * kNRedC * sizeof(R)     // per-warp partial sums
+         + (size_t)kc * kNRedC * sizeof(R)                      // cell sums
+         + (size_t)kc * sizeof(R)                               // S per cell
+         + (size_t)2 * kStages * 8 + 16;                        // full and empty mbarriers
+}
+
+template <typename R, bool ANG, bool PLM, bool ST2>
+__global__ void __launch_bounds__(kStageMaxThreads) k_stage(StageArgs a) {
   using Col = typename GeoTypes<R>::Col;
   using Face = typename GeoTypes<R>::Face;
+  using P = P2<R>;
+  using V = typename P::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = threadIdx.x;
-  const int nwarp = blockDim.x >> 5;
-  const int lane = n & 31, warp = n >> 5;
-  const bool act = n < a.nang;
+  const int t = threadIdx.x;
+  const int ncons = blockDim.x - 32;                      // consumer threads; the last warp produces
+  const bool cons = t < ncons;
+  const int nwarp = ncons >> 5;                           // consumer warps
+  const int lane = t & 31, warp = t >> 5;
+  const int b0 = 2 * t;                                   // bins b0, b0 + 1
+  const bool inpair = b0 < a.nap;                         // pair inside the padded row
+  const bool act0 = b0 < a.nang, act1 = b0 + 1 < a.nang;
   const int nchunk = (a.n3 + a.kc - 1) / a.kc;
   const int col = blockIdx.x / nchunk;
   const int chunk = blockIdx.x % nchunk;
   const int i = col % a.n1, j = col / a.n1;
   const int k0 = chunk * a.kc;
   const int nc = min(a.kc, a.n3 - k0);
-  const long long strideK = (long long)a.n1 * a.n2 * a.nap;
-  const long long ncol = (long long)a.n1 * a.n2;
+  const unsigned ncol = (unsigned)a.n1 * a.n2;
+  const unsigned strideK = ncol * (unsigned)a.nap;        // element offsets fit in 32 bits (host-checked)
   const R *Ip = (const R *)a.Iprev;
   const R *I0 = (const R *)a.I0;
   R *Io = (R *)a.Iout;
-  const bool plm = a.recon == RAD_RECON_PLM;
+  constexpr bool plm = PLM;
   const bool couple = a.mode != RAD_COUPLE_NONE;
 
-  R *sgas = (R *)smem_raw;                                 // [kMaxChunk][4]
-  R *su0 = sgas + kMaxChunk * 4;                            // [kMaxChunk]
-  R *red = su0 + kMaxChunk;                                 // [kMaxChunk][nwarp][kNRedC]
-  R *sums = red + kMaxChunk * nwarp * kNRedC;               // [kMaxChunk][kNRedC]
-  R *Sc = sums + kMaxChunk * kNRedC;                        // [kMaxChunk]
-  R *rows = Sc + kMaxChunk;                                 // [2][nap]
+  // shared memory: staged rows, I* of the chunk, then small per-cell arrays
+  R *stg = (R *)smem_raw;                                  // [kStages][kRows][nap]
+  R *sI = stg + kStages * kRows * a.nap;                   // [kc][nap]
+  R *sgas = sI + a.kc * a.nap;                             // [kc][5]
+  R *red = sgas + a.kc * 5;                                // [kc][nwarp][kNRedC]
+  R *sums = red + a.kc * nwarp * kNRedC;                   // [kc][kNRedC]
+  R *Sc = sums + a.kc * kNRedC;                            // [kc]
+  uint64_t *bars = (uint64_t *)(((uintptr_t)(Sc + a.kc) + 15) & ~(uintptr_t)15);   // [kStages] full
+  uint64_t *ebars = bars + kStages;                                                   // [kStages] empty
 
-  // ---- gas state of the chunk (one conversion per cell)
-  for (int c = n; c < nc; c += blockDim.x) {
-    long long cell = (long long)(k0 + c) * ncol + col;
+  for (int c = t; c < nc; c += blockDim.x) {
+    const unsigned cell = (unsigned)(k0 + c) * ncol + col;
     if (couple) {
-      double ux = a.u[3 * cell], uy = a.u[3 * cell + 1], uz = a.u[3 * cell + 2];
-      sgas[4 * c + 0] = (R)ux;
-      sgas[4 * c + 1] = (R)uy;
-      sgas[4 * c + 2] = (R)uz;
-      sgas[4 * c + 3] = (R)(a.aa[cell] + a.as[cell]);
-      su0[c] = (R)sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+      const double ux = a.u[3 * cell], uy = a.u[3 * cell + 1], uz = a.u[3 * cell + 2];
+      sgas[5 * c + 0] = (R)ux;
+      sgas[5 * c + 1] = (R)uy;
+      sgas[5 * c + 2] = (R)uz;
+      sgas[5 * c + 3] = (R)(a.aa[cell] + a.as[cell]);
+      sgas[5 * c + 4] = (R)sqrt(1.0 + ux * ux + uy * uy + uz * uz);
     }
   }
 
-  // ---- per-bin prefactors of this column
+  // ---- per-bin prefactors of this column (pair)
   const Col &cg = ((const Col *)a.cols)[col];
-  R nh0 = R(0), nh1 = R(0), nh2 = R(0), dOm = R(1);
-  if (act) {
-    nh0 = (R)a.dir[3 * n];
-    nh1 = (R)a.dir[3 * n + 1];
-    nh2 = (R)a.dir[3 * n + 2];
-    dOm = (R)a.dOmega[n];
+  R nx_[2] = {R(0), R(0)}, ny_[2] = {R(0), R(0)}, nz_[2] = {R(0), R(0)}, dO_[2] = {R(1), R(1)};
+  for (int e = 0; e < 2; ++e) {
+    if (b0 + e < a.nang) {
+      nx_[e] = (R)a.dir[3 * (b0 + e)];
+      ny_[e] = (R)a.dir[3 * (b0 + e) + 1];
+      nz_[e] = (R)a.dir[3 * (b0 + e) + 2];
+      dO_[e] = (R)a.dOmega[b0 + e];
+    }
   }
+  const V nhx = P::mk(nx_[0], nx_[1]), nhy = P::mk(ny_[0], ny_[1]), nhz = P::mk(nz_[0], nz_[1]);
+  const V dOm = P::mk(act0 ? dO_[0] : R(0), act1 ? dO_[1] : R(0));
   const R n0up = cg.n0up;
-  const R nlow0 = cg.M[0][0] + cg.M[0][1] * nh0 + cg.M[0][2] * nh1 + cg.M[0][3] * nh2;
-  const R fconv = n0up * nlow0;                          // U = n^0 n_0 I
-  const bool guard = act && a.zero_guard && fabs((double)nlow0) < a.n0crit;
-  const R inv_f = act ? R(1) / fconv : R(0);
+  const V nlow0 = P::fma(nhz, P::mk(cg.M[0][3], cg.M[0][3]),
+                         P::fma(nhy, P::mk(cg.M[0][2], cg.M[0][2]),
+                                P::fma(nhx, P::mk(cg.M[0][1], cg.M[0][1]), P::mk(cg.M[0][0], cg.M[0][0]))));
+  const V fconv = P::mul(P::mk(n0up, n0up), nlow0);                 // U = n^0 n_0 I
+  const bool g0 = act0 && a.zero_guard && fabs((double)nlow0.x) < a.n0crit;
+  const bool g1 = act1 && a.zero_guard && fabs((double)nlow0.y) < a.n0crit;
+  // primitive recovery factor (0 for guarded or inactive bins)
+  const V inv_f = P::mk((act0 && !g0) ? R(1) / fconv.x : R(0), (act1 && !g1) ? R(1) / fconv.y : R(0));
   const R invdV = cg.invdV;
-  auto fcoef = [&](const Face &F, bool &upR) -> R {
-    R na = F.ea[0] + F.ea[1] * nh0 + F.ea[2] * nh1 + F.ea[3] * nh2;
-    R n0 = F.m0[0] + F.m0[1] * nh0 + F.m0[2] * nh1 + F.m0[3] * nh2;
-    upR = na < R(0);
-    return F.dA * na * n0 * invdV;
+  auto fcoef = [&](const Face &F, unsigned &upR) -> V {
+    V na = P::fma(nhz, P::mk(F.ea[3], F.ea[3]),
+                  P::fma(nhy, P::mk(F.ea[2], F.ea[2]), P::fma(nhx, P::mk(F.ea[1], F.ea[1]), P::mk(F.ea[0], F.ea[0]))));
+    V n0 = P::fma(nhz, P::mk(F.m0[3], F.m0[3]),
+                  P::fma(nhy, P::mk(F.m0[2], F.m0[2]), P::fma(nhx, P::mk(F.m0[1], F.m0[1]), P::mk(F.m0[0], F.m0[0]))));
+    upR = (na.x < R(0) ? 1u : 0u) | (na.y < R(0) ? 2u : 0u);
+    V c = P::mul(P::mul(na, n0), P::mk(F.dA * invdV, F.dA * invdV));
+    return P::mk(act0 ? c.x : R(0), act1 ? c.y : R(0));
   };
-  R cm[3] = {R(0), R(0), R(0)}, cp[3] = {R(0), R(0), R(0)};
-  bool um[3] = {false, false, false}, up[3] = {false, false, false};
-  if (act) {
+  V cm[3], cp[3];
+  unsigned um[3] = {0u, 0u, 0u}, up[3] = {0u, 0u, 0u};
+  for (int d = 0; d < 3; ++d) cm[d] = cp[d] = P::mk(R(0), R(0));
+  {
     const Face *F1 = (const Face *)a.f1, *F2 = (const Face *)a.f2, *F3 = (const Face *)a.f3;
     cm[0] = fcoef(F1[j * (a.n1 + 1) + i], um[0]);
     cp[0] = fcoef(F1[j * (a.n1 + 1) + i + 1], up[0]);
@@ -268,159 +386,248 @@ __global__ void __launch_bounds__(MAXT) k_stage(StageArgs a) {
       up[2] = um[2];
     }
   }
-  // angular flux: divA_n = a_self I_n + sum_s a_nb[s] I_{m_s}
-  R a_self = R(0);
-  R a_nb[kMaxSlots];
-  int nb_m[kMaxSlots];
+  // angular flux of each bin: divA = a_self I + sum_s a_nb[s] I_{m_s}
+  R a_self[2] = {R(0), R(0)}, a_nb[2][kMaxSlots];
+  int nb_m[2][kMaxSlots];
   if (ANG) {
-    R self = R(0);
+    for (int e = 0; e < 2; ++e) {
+      const int n = b0 + e;
+      const bool ac = n < a.nang;
+      R self = R(0);
 #pragma unroll
-    for (int s = 0; s < kMaxSlots; ++s) {
-      a_nb[s] = R(0);
-      nb_m[s] = act ? n : 0;
-      int m = act ? a.slot_nbr[6 * n + s] : -1;
-      if (m < 0) continue;
-      nb_m[s] = m;
-      int e = a.slot_edge[6 * n + s];
-      const double *eg = a.edge_geo + 8 * e;
-      R x = (R)eg[0], y = (R)eg[1], z = (R)eg[2], v0 = (R)eg[3], v1 = (R)eg[4], v2 = (R)eg[5], len = (R)eg[6];
-      R pr[10] = {R(1), x, y, z, x * x, x * y, x * z, y * y, y * z, z * z};
-      R q0 = R(0), q1 = R(0), q2 = R(0);
+      for (int s = 0; s < kMaxSlots; ++s) {
+        a_nb[e][s] = R(0);
+        nb_m[e][s] = ac ? n : 0;
+        int m = ac ? a.slot_nbr[6 * n + s] : -1;
+        if (m < 0) continue;
+        nb_m[e][s] = m;
+        int ed = a.slot_edge[6 * n + s];
+        const double *eg = a.edge_geo + 8 * ed;
+        R x = (R)eg[0], y = (R)eg[1], z = (R)eg[2], v0 = (R)eg[3], v1 = (R)eg[4], v2 = (R)eg[5], len = (R)eg[6];
+        R pr[10] = {R(1), x, y, z, x * x, x * y, x * z, y * y, y * z, z * z};
+        R q0 = R(0), q1 = R(0), q2 = R(0);
 #pragma unroll
-      for (int p = 0; p < 10; ++p) {
-        q0 += cg.K[0][p] * pr[p];
-        q1 += cg.K[1][p] * pr[p];
-        q2 += cg.K[2][p] * pr[p];
+        for (int p = 0; p < 10; ++p) {
+          q0 += cg.K[0][p] * pr[p];
+          q1 += cg.K[1][p] * pr[p];
+          q2 += cg.K[2][p] * pr[p];
+        }
+        R sp = -(v0 * q0 + v1 * q1 + v2 * q2);          // V . nu (nu is normal to n_e)
+        R n0e = cg.M[0][0] + cg.M[0][1] * x + cg.M[0][2] * y + cg.M[0][3] * z;
+        R Pv = len * sp * n0e;
+        R PL = sp >= R(0) ? Pv : R(0), PR = sp >= R(0) ? R(0) : Pv;
+        R dOn = e ? dO_[1] : dO_[0];
+        if (a.edge_pq[2 * ed] == n) {
+          self += PL;
+          a_nb[e][s] = PR / dOn;
+        } else {
+          self -= PR;
+          a_nb[e][s] = -PL / dOn;
+        }
       }
-      R sp = -(v0 * q0 + v1 * q1 + v2 * q2);           // V . nu (nu is normal to n_e)
-      R n0e = cg.M[0][0] + cg.M[0][1] * x + cg.M[0][2] * y + cg.M[0][3] * z;
-      R P = len * sp * n0e;
-      R PL = sp >= R(0) ? P : R(0), PR = sp >= R(0) ? R(0) : P;
-      if (a.edge_pq[2 * e] == n) {
-        self += PL;
-        a_nb[s] = PR / dOm;
-      } else {
-        self -= PR;
-        a_nb[s] = -PL / dOm;
-      }
+      a_self[e] = ac ? self / (e ? dO_[1] : dO_[0]) : R(0);
     }
-    a_self = act ? self / dOm : R(0);
   }
-  // x1 / x2 neighbours of this column
-  Nbr nx[4], ny[4];
+  // ---- stencil rows of one cell: the contiguous x1 block (rows i-2..i+2, or
+  // one copy per row at a boundary), the four x2 rows, this column's row at
+  // k+2 (x3 window) and, in stage 2, this column's row of I^0.
+  // Slots: 0..4 x1 block (2 = own), 5..8 x2 rows j-2, j-1, j+1, j+2, 9 own k+2, 10 I^0.
   const int offs[4] = {-2, -1, 1, 2};
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
+  int xs[5], yj[4], ypol[4];
+  bool x1contig = true;
+  for (int q = 0; q < 5; ++q) {
     int pol;
-    int ii = wrap_idx(i + offs[t], a.n1, a.bc_lo[0], a.bc_hi[0], pol);
-    nx[t].col_off = ((long long)j * a.n1 + ii) * a.nap;
-    nx[t].kshift = 0;
-    nx[t].polar = 0;
-    int jj = j;
-    pol = 0;
-    if (a.ndim >= 2) jj = wrap_idx(j + offs[t], a.n2, a.bc_lo[1], a.bc_hi[1], pol);
-    ny[t].col_off = ((long long)jj * a.n1 + i) * a.nap;
-    ny[t].kshift = pol ? a.n3 / 2 : 0;
-    ny[t].polar = pol;
+    xs[q] = q == 2 ? i : wrap_idx(i + q - 2, a.n1, a.bc_lo[0], a.bc_hi[0], pol);
+    if (xs[q] != i + q - 2) x1contig = false;
   }
-  const int nperm = act ? a.perm[n] : 0;
-  const int nself = act ? n : 0;
-  const long long own = (long long)col * a.nap + nself;
+  bool anypol = false;
+  for (int q = 0; q < 4; ++q) {
+    int pol = 0;
+    yj[q] = a.ndim >= 2 ? wrap_idx(j + offs[q], a.n2, a.bc_lo[1], a.bc_hi[1], pol) : j;
+    ypol[q] = pol;
+    anypol |= pol != 0;
+  }
+  const bool d3 = a.ndim >= 3;
+  const size_t rowb = (size_t)a.nap * sizeof(R);
   auto kidx = [&](int k) {
     int pol;
     return wrap_idx(k, a.n3, a.bc_lo[2], a.bc_hi[2], pol);
   };
-  auto ld_nb = [&](const Nbr &nb, int k) -> R {
-    int kk = k + nb.kshift;
-    if (kk >= a.n3) kk -= a.n3;
-    return __ldg(Ip + (long long)kk * strideK + nb.col_off + (nb.polar ? nperm : nself));
+  auto rowp = [&](const R *base, int ii, int jj, int kk) {
+    return base + ((size_t)kk * ncol + (size_t)jj * a.n1 + ii) * a.nap;
   };
-  const R dtR = (R)a.dt, dts = (R)a.dts;
-  const R c2pre = dts / R(kFourPi);
-  __syncthreads();   // gas staged
-
-  // ---- phase A
-  R win[5];
-  const bool d3 = a.ndim >= 3;
-  if (d3) {
-#pragma unroll
-    for (int t = 0; t < 4; ++t) win[t + 1] = __ldg(Ip + (long long)kidx(k0 - 2 + t) * strideK + own);
-  }
-  for (int c = 0; c < nc; ++c) {
+  auto produce = [&](int c) {      // thread 0: issue the copies of cell k0 + c
+    const int st = c % kStages;
     const int k = k0 + c;
-    R zc, sx = R(0);
-    if (d3) {
-#pragma unroll
-      for (int t = 0; t < 4; ++t) win[t] = win[t + 1];
-      win[4] = __ldg(Ip + (long long)kidx(k + 2) * strideK + own);
-      zc = win[2];
-      R lo = face_val(um[2], plm, win[0], win[1], win[2], win[3]);
-      R hi = face_val(up[2], plm, win[1], win[2], win[3], win[4]);
-      sx = cp[2] * hi - cm[2] * lo;
+    R *dst = stg + (size_t)st * kRows * a.nap;
+    uint32_t bytes = (uint32_t)(5 * rowb) + (a.ndim >= 2 ? (uint32_t)(4 * rowb) : 0u) +
+                     (d3 ? (uint32_t)rowb : 0u) + (ST2 ? (uint32_t)rowb : 0u);
+    mbar_expect_tx(&bars[st], bytes);
+    if (x1contig) {
+      bulk_g2s(dst, rowp(Ip, i - 2, j, k), (uint32_t)(5 * rowb), &bars[st]);
     } else {
-      zc = __ldg(Ip + (long long)k * strideK + own);
-    }
-    {
-      R m2 = ld_nb(nx[0], k), m1 = ld_nb(nx[1], k), p1 = ld_nb(nx[2], k), p2 = ld_nb(nx[3], k);
-      sx += cp[0] * face_val(up[0], plm, m1, zc, p1, p2) - cm[0] * face_val(um[0], plm, m2, m1, zc, p1);
+      for (int q = 0; q < 5; ++q) bulk_g2s(dst + q * a.nap, rowp(Ip, xs[q], j, k), (uint32_t)rowb, &bars[st]);
     }
     if (a.ndim >= 2) {
-      R m2 = ld_nb(ny[0], k), m1 = ld_nb(ny[1], k), p1 = ld_nb(ny[2], k), p2 = ld_nb(ny[3], k);
-      sx += cp[1] * face_val(up[1], plm, m1, zc, p1, p2) - cm[1] * face_val(um[1], plm, m2, m1, zc, p1);
+      for (int q = 0; q < 4; ++q) {
+        int kk = k;
+        if (ypol[q] && a.n3 > 1) kk = (k + a.n3 / 2) % a.n3;
+        bulk_g2s(dst + (5 + q) * a.nap, rowp(Ip, i, yj[q], kk), (uint32_t)rowb, &bars[st]);
+      }
     }
-    R divA = R(0);
-    if (ANG) {
-      R *row = rows + (c & 1) * a.nap;
-      if (n < a.nap) row[n] = zc;
-      __syncthreads();
-      divA = a_self * zc;
-#pragma unroll
-      for (int s = 0; s < kMaxSlots; ++s) divA += a_nb[s] * row[nb_m[s]];
+    if (d3) bulk_g2s(dst + 9 * a.nap, rowp(Ip, i, j, kidx(k + 2)), (uint32_t)rowb, &bars[st]);
+    if (ST2) bulk_g2s(dst + 10 * a.nap, rowp(I0, i, j, k), (uint32_t)rowb, &bars[st]);
+  };
+  const int p0 = act0 ? a.perm[b0] : 0, p1 = act1 ? a.perm[b0 + 1] : 0;
+  const unsigned own = (unsigned)col * a.nap + (inpair ? b0 : 0);
+  const int bb = inpair ? b0 : 0;
+  auto sv = [&](const R *row) -> V { return *(const V *)(row + bb); };
+  const R dtR = (R)a.dt, dts = (R)a.dts;
+  const R c2pre = dts / R(kFourPi);
+  const V zero = P::mk(R(0), R(0));
+  if (t == 0) {
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(&bars[st], 1);
+      mbar_init(&ebars[st], (uint32_t)nwarp);
     }
-    const R L = -(sx + divA);
-    const R Uprev = fconv * zc;
-    R Us;
-    if (a.stage2) {
-      R U0 = fconv * (act ? I0[(long long)k * strideK + own] : R(0));
-      Us = R(0.5) * U0 + R(0.5) * (Uprev + dtR * L);
-    } else {
-      Us = Uprev + dtR * L;
-    }
-    const R Is = (guard || !act) ? R(0) : Us * inv_f;
-    if (act) {
-      Io[(long long)k * strideK + own] = Is;
-      if (a.Istar) ((R *)a.Istar)[(long long)k * strideK + own] = Is;
-    }
-    if (couple) {
-      const R ux = sgas[4 * c], uy = sgas[4 * c + 1], uz = sgas[4 * c + 2], aE = sgas[4 * c + 3];
-      const R nb = su0[c] - (ux * nh0 + uy * nh1 + uz * nh2);
-      const R rden = fdiv(R(1), n0up + nb * aE * dts);
-      const R w = Is * nb * nb * dOm;                      // Ibar dOmega_bar
-      // A1 - Ebar = sum (c1 - 1) Ibar dOmega_bar, A2' = sum dOmega / (n^0bar den), Ebar
-      R v0 = act ? -(nb * aE * dts) * rden * w : R(0);
-      R v1 = act ? fdiv(dOm * rden, nb) : R(0);
-      R v2 = act ? w : R(0);
-      R s = warp_reduce4(v0, v1, v2, R(0), lane);
-      if ((lane & 7) == 0 && lane < 24) red[(c * nwarp + warp) * kNRedC + (lane >> 3)] = s;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();   // gas staged, barriers initialised
+  bool timeout = false;
+  if (!cons) {
+    // ---- producer warp: one lane issues every cell's copies into the ring,
+    // waiting for the consumers to release a stage before refilling it
+    if (lane == 0) {
+      for (int c = 0; c < nc; ++c) {
+        const int st = c % kStages;
+        if (c >= kStages && !mbar_wait_parity(&ebars[st], (uint32_t)(((c / kStages) - 1) & 1))) {
+          timeout = true;     // the consumers time out on the full barrier in turn
+          break;
+        }
+        produce(c);
+      }
     }
   }
+
+  // ---- phase A (consumer warps): transport, stage combination, primitive I*, coupling sums
+  V w0 = zero, w1 = zero, w2 = zero, w3 = zero, qa = zero, qb = zero;   // x3 window and slopes
+  if (cons && d3) {
+    w0 = __ldg((const V *)(Ip + (unsigned)kidx(k0 - 2) * strideK + own));
+    w1 = __ldg((const V *)(Ip + (unsigned)kidx(k0 - 1) * strideK + own));
+    w2 = __ldg((const V *)(Ip + (unsigned)kidx(k0) * strideK + own));
+    w3 = __ldg((const V *)(Ip + (unsigned)kidx(k0 + 1) * strideK + own));
+    if (plm) {
+      qa = vl2<R>(w0, w1, w2);
+      qb = vl2<R>(w1, w2, w3);
+    }
+  }
+  for (int c = 0; c < (cons ? nc : 0); ++c) {
+    const int st = c % kStages;
+    const R *sr = stg + (size_t)st * kRows * a.nap;
+    if (!mbar_wait_parity(&bars[st], (uint32_t)((c / kStages) & 1))) timeout = true;
+    V zc, sx = zero;
+    if (d3) {
+      const V w4 = sv(sr + 9 * a.nap);
+      const V qc = plm ? vl2<R>(w2, w3, w4) : zero;   // slope of k+1
+      zc = w2;
+      // slopes: qa = slope(k-1), qb = slope(k), qc = slope(k+1)
+      sx = face_div<R>(um[2], up[2], cm[2], cp[2], w1, w2, w3, qa, qb, qc);
+      w0 = w1;
+      w1 = w2;
+      w2 = w3;
+      w3 = w4;
+      qa = qb;
+      qb = qc;
+    } else {
+      zc = sv(sr + 2 * a.nap);
+    }
+    {
+      const V m2 = sv(sr), m1 = sv(sr + a.nap), q1 = sv(sr + 3 * a.nap), q2 = sv(sr + 4 * a.nap);
+      V sm = zero, sc = zero, sp = zero;
+      if (plm) {
+        sm = vl2<R>(m2, m1, zc);
+        sc = vl2<R>(m1, zc, q1);
+        sp = vl2<R>(zc, q1, q2);
+      }
+      sx = P::add(sx, face_div<R>(um[0], up[0], cm[0], cp[0], m1, zc, q1, sm, sc, sp));
+    }
+    if (a.ndim >= 2) {
+      V yv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const R *row = sr + (5 + q) * a.nap;
+        yv[q] = (anypol && ypol[q]) ? P::mk(row[p0], row[p1]) : sv(row);
+      }
+      V sm = zero, sc = zero, sp = zero;
+      if (plm) {
+        sm = vl2<R>(yv[0], yv[1], zc);
+        sc = vl2<R>(yv[1], zc, yv[2]);
+        sp = vl2<R>(zc, yv[2], yv[3]);
+      }
+      sx = P::add(sx, face_div<R>(um[1], up[1], cm[1], cp[1], yv[1], zc, yv[2], sm, sc, sp));
+    }
+    V divA = zero;
+    if (ANG) {
+      // the own row of this cell is slot 2 of the staged x1 block
+      const R *row = sr + 2 * a.nap;
+      R da[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        R acc = a_self[e] * (e ? zc.y : zc.x);
+#pragma unroll
+        for (int s2 = 0; s2 < kMaxSlots; ++s2) acc += a_nb[e][s2] * row[nb_m[e][s2]];
+        da[e] = acc;
+      }
+      divA = P::mk(da[0], da[1]);
+    }
+    // U* = U^{s-1} + dt L   (stage 1)   or   U^0/2 + (U^1 + dt L)/2   (stage 2), L = -(divS + divA)
+    const V L = P::mk(-(sx.x + divA.x), -(sx.y + divA.y));
+    V Us = P::fma(P::mk(dtR, dtR), L, P::mul(fconv, zc));
+    if (ST2) {
+      const V U0 = P::mul(fconv, sv(sr + 10 * a.nap));
+      Us = P::mul(P::mk(R(0.5), R(0.5)), P::add(U0, Us));
+    }
+    const V Is = P::mul(Us, inv_f);
+    if (inpair) *(V *)(sI + c * a.nap + b0) = Is;
+    if (a.Istar && inpair) *(V *)((R *)a.Istar + (unsigned)(k0 + c) * strideK + own) = Is;
+    if (couple) {
+      const R *g = sgas + 5 * c;
+      const V ux = P::mk(g[0], g[0]), uy = P::mk(g[1], g[1]), uz = P::mk(g[2], g[2]);
+      const R aEd = g[3] * dts;
+      const V nb = P::sub(P::mk(g[4], g[4]), P::fma(uz, nhz, P::fma(uy, nhy, P::mul(ux, nhx))));
+      const V nbaE = P::mul(nb, P::mk(aEd, aEd));
+      const V rden = P::rcp(P::add(P::mk(n0up, n0up), nbaE));
+      const V w = P::mul(P::mul(Is, P::mul(nb, nb)), dOm);                 // Ibar dOmega_bar
+      const V v0 = P::mul(P::mul(P::mk(-nbaE.x, -nbaE.y), rden), w);     // (c1 - 1) Ibar dOmega_bar
+      const V v1 = P::mul(P::mul(dOm, rden), P::rcp(nb));                 // dOmega / (n^0bar den)
+      const R s2 = warp_reduce4(v0.x + v0.y, v1.x + v1.y, w.x + w.y, R(0), lane);
+      if ((lane & 7) == 0 && lane < 24) red[(c * nwarp + warp) * kNRedC + (lane >> 3)] = s2;
+    }
+    // this warp is done with the stage: release it to the producer
+    __syncwarp();
+    if (lane == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&ebars[st])) : "memory");
+    }
+  }
+  if (timeout) atomicOr(a.err, 1 << 3);
 
   if (couple) {
     __syncthreads();
     // ---- phase B: one thread per cell
-    for (int t = n; t < nc * kNRedA; t += blockDim.x) {
-      int c = t / kNRedA, r = t % kNRedA;
+    for (int q = t; q < nc * kNRedA; q += blockDim.x) {
+      const int c = q / kNRedA, r = q % kNRedA;
       R s = R(0);
       for (int w = 0; w < nwarp; ++w) s += red[(c * nwarp + w) * kNRedC + r];
       sums[c * kNRedC + r] = s;
     }
     __syncthreads();
-    if (n < nc) {
-      const int c = n, k = k0 + c;
-      const long long cell = (long long)k * ncol + col;
+    if (t < nc) {
+      const int c = t, k = k0 + c;
+      const unsigned cell = (unsigned)k * ncol + col;
       const R *rs = sums + c * kNRedC;
       const double D = (double)rs[0], A2 = a.dts / kFourPi * (double)rs[1], Em = (double)rs[2];
-      const double Tst = a.stage2 ? 0.5 * (a.T0[cell] + a.T1[cell]) : a.T0[cell];
+      const double Tst = ST2 ? 0.5 * (a.T0[cell] + a.T1[cell]) : a.T0[cell];
       const double aa = a.aa[cell], as = a.as[cell];
       double S, Tp = Tst;
       bool ok = true;
@@ -445,60 +652,65 @@ __global__ void __launch_bounds__(MAXT) k_stage(StageArgs a) {
       a.Tout[cell] = Tp;
     }
     __syncthreads();
-  } else if (n < nc) {
-    const long long cell = (long long)(k0 + n) * ncol + col;
-    a.Tout[cell] = a.stage2 ? 0.5 * (a.T0[cell] + a.T1[cell]) : a.T0[cell];
-    if (a.src && !a.stage2) {
-      for (int m = 0; m < 4; ++m) a.src[4 * cell + m] = 0.0;
+  } else {
+    __syncthreads();
+    if (t < nc) {
+      const unsigned cell = (unsigned)(k0 + t) * ncol + col;
+      a.Tout[cell] = ST2 ? 0.5 * (a.T0[cell] + a.T1[cell]) : a.T0[cell];
+      if (a.src && !ST2) {
+        for (int m = 0; m < 4; ++m) a.src[4 * cell + m] = 0.0;
+      }
     }
   }
 
   // ---- phase C: implicit update of every bin
   bool bad = false;
   const bool want_src = couple && a.src;
-  for (int c = 0; c < nc; ++c) {
-    const int k = k0 + c;
-    R *po = Io + (long long)k * strideK + own;
-    R Is = act ? *po : R(0);
-    R out = Is;
+  for (int c = 0; c < (cons ? nc : 0); ++c) {
+    const unsigned kOff = (unsigned)(k0 + c) * strideK;
+    const V Is = inpair ? *(const V *)(sI + c * a.nap + b0) : zero;
+    V out = Is;
     if (couple) {
-      const R ux = sgas[4 * c], uy = sgas[4 * c + 1], uz = sgas[4 * c + 2], aE = sgas[4 * c + 3];
-      const R nb = su0[c] - (ux * nh0 + uy * nh1 + uz * nh2);
-      const R rden = fdiv(R(1), n0up + nb * aE * dts);
-      const R c2n = fdiv(c2pre * rden, nb * nb * nb);     // c2 / (n^0bar)^4
-      out = n0up * rden * Is + c2n * Sc[c];
+      const R *g = sgas + 5 * c;
+      const V ux = P::mk(g[0], g[0]), uy = P::mk(g[1], g[1]), uz = P::mk(g[2], g[2]);
+      const R aEd = g[3] * dts;
+      const V nb = P::sub(P::mk(g[4], g[4]), P::fma(uz, nhz, P::fma(uy, nhy, P::mul(ux, nhx))));
+      const V rden = P::rcp(P::fma(nb, P::mk(aEd, aEd), P::mk(n0up, n0up)));
+      const V c2n = P::mul(P::mul(P::mk(c2pre, c2pre), rden), P::rcp(P::mul(nb, P::mul(nb, nb))));
+      out = P::fma(P::mul(P::mk(n0up, n0up), rden), Is, P::mul(c2n, P::mk(Sc[c], Sc[c])));
+      if (want_src) {
+        // gas source: sums of (I+ - I*) n^A dOmega (taken before the guard)
+        const V d = P::mul(P::sub(out, Is), dOm);
+        const V dx = P::mul(d, nhx), dy = P::mul(d, nhy), dz = P::mul(d, nhz);
+        const R s = warp_reduce4(d.x + d.y, dx.x + dx.y, dy.x + dy.y, dz.x + dz.y, lane);
+        if ((lane & 7) == 0) red[(c * nwarp + warp) * kNRedC + (lane >> 3)] = s;
+      }
     }
-    if (want_src) {
-      // gas source: sums of (I+ - I*) n^A dOmega (taken before the guard)
-      R d = act ? (out - Is) * dOm : R(0);
-      R s = warp_reduce4(d, d * nh0, d * nh1, d * nh2, lane);
-      if ((lane & 7) == 0) red[(c * nwarp + warp) * kNRedC + (lane >> 3)] = s;
-    }
-    if (guard) out = R(0);
-    if (act) {
-      *po = out;
-      bad |= !isfinite(out);
+    out = P::mk((act0 && !g0) ? out.x : R(0), (act1 && !g1) ? out.y : R(0));
+    if (inpair) {
+      *(V *)(Io + kOff + own) = out;
+      bad |= !isfinite(out.x) || !isfinite(out.y);
     }
   }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrNonFinite);
+  if (cons && __any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrNonFinite);
   if (want_src) {
     // ---- phase D: -dR^0_mu with dR^0_mu = n^0 M[mu][A] sum (I+ - I*) n^A dOmega
     __syncthreads();
-    if (n < nc) {
-      const int c = n;
-      const long long cell = (long long)(k0 + c) * ncol + col;
+    if (t < nc) {
+      const int c = t;
+      const unsigned cell = (unsigned)(k0 + c) * ncol + col;
       R xs[4];
 #pragma unroll
       for (int A = 0; A < 4; ++A) {
-        R t = R(0);
-        for (int w = 0; w < nwarp; ++w) t += red[(c * nwarp + w) * kNRedC + A];
-        xs[A] = t;
+        R s = R(0);
+        for (int w = 0; w < nwarp; ++w) s += red[(c * nwarp + w) * kNRedC + A];
+        xs[A] = s;
       }
       double *sp = a.src + 4 * cell;
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         R dR = n0up * (cg.M[m][0] * xs[0] + cg.M[m][1] * xs[1] + cg.M[m][2] * xs[2] + cg.M[m][3] * xs[3]);
-        sp[m] = a.stage2 ? sp[m] - (double)dR : -0.5 * (double)dR;
+        sp[m] = ST2 ? sp[m] - (double)dR : -0.5 * (double)dR;
       }
     }
   }
