@@ -16,6 +16,7 @@ the workload on its own GPU (no halo exchange is built), and value is the
 sum over ranks.
 """
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -35,13 +36,15 @@ WORKLOAD = "turb3d"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
-    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--precision", default="f32", choices=["f32", "f64"])
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--n", type=int, default=None, help="cells per side (default: the workload's 128)")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the FP64-path, accuracy and adjoint/forward measurements")
     return p.parse_args()
 
 
@@ -54,7 +57,8 @@ def peaks():
 
 # --------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+    """nvidia-smi samples (every 100 ms), each stamped with the host clock on
+    arrival; summary() keeps those that arrived inside the timed window."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -64,11 +68,12 @@ class ClockSampler:
         self.index = index
         self.rows = []
         self.proc = None
+        self.window = (0.0, float("inf"))
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -78,7 +83,14 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append((time.perf_counter(), [x.strip() for x in line.split(",")]))
+
+    def ready(self, timeout=10.0):
+        """Wait for the first sample: nvidia-smi's start-up must not fall
+        inside the timed region."""
+        t0 = time.perf_counter()
+        while self.proc and not self.rows and time.perf_counter() - t0 < timeout:
+            time.sleep(0.05)
 
     def __exit__(self, *a):
         if self.proc:
@@ -89,23 +101,23 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        lo, hi = self.window
+        rows = [r for (t, r) in self.rows if lo <= t <= hi]
+        if not rows:         # window shorter than one sampling period: nearest samples
+            rows = [r for (t, r) in sorted(self.rows, key=lambda x: abs(x[0] - 0.5 * (lo + hi)))[:2]]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = sorted(float(r[1]) for r in rows if len(r) > 2)
+        mx = max(float(r[2]) for r in rows if len(r) > 2)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
-            try:
-                sm.append(float(r[1]))
-                mx = float(r[2])
-                for nm, v in zip(names, r[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(nm)
-            except Exception:
-                pass
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        reasons = set()
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(rows)}
 
 
-# ------------------------------------------------------------- our arm
 def setup_gpu(prec, dev, n=None):
     import torch
     import paper_2302_04283_gb300 as rad
@@ -130,6 +142,42 @@ def setup_gpu(prec, dev, n=None):
     return rad, w, ctx, na, nap, dt, sh, tdt, I, gas
 
 
+PROFILE = os.path.join(ROOT, "profiles", "k_stage_turb3d_f32.md")
+
+
+def kernel_fingerprint():
+    """Hash of the code lines (comments and blank lines dropped) of the stage
+    kernel and its launcher: a profile's counters describe this kernel only
+    while the fingerprint it records matches."""
+    h = hashlib.sha256()
+    for f in ("step_kernel.cuh", "step.cu"):
+        with open(os.path.join(ROOT, "paper_2302_04283_gb300", "csrc", f)) as fh:
+            for line in fh:
+                code = line.split("//")[0].strip()
+                if code:
+                    h.update(code.encode() + b"\n")
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(precision, ncell):
+    """DRAM bytes per k_stage launch (average of the two stages) from the
+    committed ncu summary, scaled by cells to this grid; None when the
+    summary is missing, was taken on another precision, or the kernel has
+    changed since."""
+    try:
+        kv = {}
+        with open(PROFILE) as fh:
+            for line in fh:
+                if line.startswith("- ") and ":" in line:
+                    k, v = line[2:].split(":", 1)
+                    kv[k.strip()] = v.strip().strip("`")
+        if kv.get("fingerprint") != kernel_fingerprint() or kv.get("precision") != precision:
+            return None
+        return float(kv["dram_bytes_per_launch"]) * ncell / float(kv["cells"])
+    except Exception:
+        return None
+
+
 def run_ours(args, rank, world):
     import torch
     dev = f"cuda:{int(os.environ.get('LOCAL_RANK', 0))}"
@@ -144,10 +192,6 @@ def run_ours(args, rank, world):
     R = torch.zeros(sh + (10,), dtype=tdt, device=dev)
     I0 = I.clone()
     T0 = gas["T"].clone()
-    try:
-        rad.rad_moments(ctx, I, prec, rad.RAD_FRAME_TETRAD, mom, gas, R)
-    except rad.RadError:
-        mom = rad.RAD_MOM_SIMT
     st = torch.cuda.current_stream()
 
     def step(ev=None):
@@ -160,28 +204,32 @@ def run_ours(args, rank, world):
         if ev:
             ev[2].record(st)
 
-    for _ in range(args.warmup):
-        step()
-    rad.rad_check(ctx)
-    # reset the state so every run times the same steps of the same workload
-    I.copy_(I0)
-    gas["T"].copy_(T0)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk:
+        clk.ready()
+        for _ in range(args.warmup):
+            step()
+        rad.rad_check(ctx)
+        # reset the state so every run times the same steps of the same workload
+        I.copy_(I0)
+        gas["T"].copy_(T0)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         start.record(st)
         for s in range(args.steps):
             step(evs[s])
         stop.record(st)
         torch.cuda.synchronize()
+        clk.window = (t0, time.perf_counter())
     if world > 1:
         torch.distributed.barrier()
     total_ms = start.elapsed_time(stop)
     stage_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
     mom_ms = sum(e[1].elapsed_time(e[2]) for e in evs)
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
     rad.rad_check(ctx)
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -193,16 +241,19 @@ def run_ours(args, rank, world):
     # stage 1 reads I^0, writes I^1; stage 2 reads I^1 and I^0, writes I^2;
     # per cell: gas fields rho, u(3), alpha_a, alpha_s and T in/out, the
     # stage temperature, and the 4-vector source)
-    bytes_stage = ncell * na * 5 * esz + ncell * 8 * (6 + 2 + 2 + 1 + 4 + 4)
-    achieved = bytes_stage * args.steps / (stage_ms * 1e-3) / 1e9
+    bytes_step = ncell * na * 5 * esz + ncell * 8 * (6 + 2 + 2 + 1 + 4 + 4)
+    achieved = bytes_step * args.steps / (stage_ms * 1e-3) / 1e9
     pk = peaks()
     hbm = pk.get("hbm_gbs")
+    traffic = profiled_traffic(args.precision, ncell)
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm or 6800.0,
             "unit": "GB/s", "frac": round(achieved / (hbm or 6800.0), 4),
-            "traffic": None, "kernel": "k_stage (both RK2 stages)",
+            "traffic": None if traffic is None else round(traffic),
+            "kernel": "k_stage (per launch: mean of the stage-1 and stage-2 launches)",
+            "algorithmic_bytes_per_launch": bytes_step // 2,
             "peak_source": "measured" if hbm else "fallback"}
     if args.precision == "f64":
-        roof["note"] = "FP64 path: bound by the FP64 pipe (see DESIGN.md), HBM fraction shown for reference"
+        roof["note"] = "FP64 path: bound by the FP64 pipe, HBM fraction shown for reference"
     res = {
         "metric": "cell-angle updates/sec", "value": value, "unit": "cell-angle updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -213,17 +264,110 @@ def run_ours(args, rank, world):
                                "moving gas |v|<=0.5, log-uniform opacities, PLM, thermal coupling",
                    "cells": ncell, "bins": na, "precision": args.precision,
                    "moments": "split-bf16 tensor cores" if mom == rad.RAD_MOM_BF16X3 else "CUDA cores",
-                   "l2": "inputs larger than L2 (I is %.2f GB)" % (ncell * nap * esz / 1e9),
+                   "l2": "inputs larger than L2 (I is %.2f GB), no flush" % (ncell * nap * esz / 1e9),
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "gpu_launches": 3 * args.steps,
         "clocks": clk.summary(),
-        "breakdown_ms_per_step": {"rad_step": stage_ms / args.steps, "rad_moments": mom_ms / args.steps},
+        "breakdown_ms_per_step": {"rad_step": stage_ms / args.steps, "rad_moments": mom_ms / args.steps,
+                                  "step_min": min(step_ms), "step_median": sorted(step_ms)[len(step_ms) // 2],
+                                  "step_max": max(step_ms)},
     }
     if not args.no_e2e:
         res["e2e"] = run_e2e(args, rad, ctx, dt, opts, prec, mom, sh, na, nap, tdt, dev, world)
     rad.rad_destroy(ctx)
+    if not args.no_extras and rank == 0 and args.precision == "f32":
+        res["extras"] = run_extras(args, dev)
     return res
+
+
+def _time_steps(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_extras(args, dev):
+    """Measurements that complete the metric: the plain FP64 path on the same
+    workload, the FP32 / split-BF16 error against the FP64 path after one step
+    (the FP64 path matches the FP64 oracle to 1e-12, a parity test), and the
+    adjoint/forward time ratio on the 2D Kerr-Schild adjoint workload."""
+    import torch
+    out = {}
+    rad, w, ctx, na, nap, dt, sh, _, I32, gas = setup_gpu("f32", dev, args.n)
+    I64 = torch.zeros(sh + (nap,), dtype=torch.float64, device=dev)
+    I64[..., :na] = I32[..., :na].double()      # same initial state on both paths
+    I32[..., :na] = I64[..., :na].float()
+    T0 = gas["T"].clone()
+    ncell = sh[0] * sh[1] * sh[2]
+    o64 = rad.rad_opts_default(precision=rad.RAD_F64)
+    o32 = rad.rad_opts_default(precision=rad.RAD_F32)
+    # accuracy after one step from the same state
+    g64 = dict(gas, T=T0.clone())
+    g32 = dict(gas, T=T0.clone())
+    a64, a32 = I64.clone(), I32.clone()
+    rad.rad_step(ctx, a64, g64, dt, o64)
+    rad.rad_step(ctx, a32, g32, dt, o32)
+    R64 = torch.zeros(sh + (10,), dtype=torch.float64, device=dev)
+    R32 = torch.zeros(sh + (10,), dtype=torch.float32, device=dev)
+    rad.rad_moments(ctx, a64, rad.RAD_F64, rad.RAD_FRAME_TETRAD, rad.RAD_MOM_SIMT, g64, R64)
+    rad.rad_moments(ctx, a32, rad.RAD_F32, rad.RAD_FRAME_TETRAD, rad.RAD_MOM_BF16X3, g32, R32)
+    torch.cuda.synchronize()
+    rad.rad_check(ctx)
+    dI = (a32[..., :na].double() - a64[..., :na]).abs().max() / a64[..., :na].abs().max()
+    dT = ((g32["T"] - g64["T"]).abs() / g64["T"].abs()).max()
+    dR = ((R32.double() - R64).abs() / R64[..., :1].abs()).max()
+    out["f32_vs_f64_after_1_step"] = {"I_rel_max": float(dI), "T_rel_max": float(dT),
+                                      "R_over_R00_max": float(dR),
+                                      "stated_tolerance": {"I": 2e-5, "T": 2e-5, "R": 1.5e-4}}
+    del a64, a32, R32
+    # plain FP64 path, same workload
+    Rb = torch.zeros(sh + (10,), dtype=torch.float64, device=dev)
+
+    def s64():
+        rad.rad_step(ctx, I64, gas, dt, o64)
+        rad.rad_moments(ctx, I64, rad.RAD_F64, rad.RAD_FRAME_TETRAD, rad.RAD_MOM_SIMT, gas, Rb)
+
+    gas["T"].copy_(T0)
+    ms64 = _time_steps(s64, 3, 1)
+    rad.rad_check(ctx)
+    out["f64_plain"] = {"value": ncell * na / (ms64 * 1e-3), "unit": "cell-angle updates/s", "ms_per_step": ms64,
+                        "what": "rad_step FP64 + rad_moments FP64 on CUDA cores, same workload, 3 steps"}
+    rad.rad_destroy(ctx)
+    del I64, I32, Rb
+    # adjoint / forward on the adjoint workload (FP64, fixed emissivity)
+    import workloads as W
+    wa = W.make("adjoint2d", with_intensity=False)
+    ctx = rad.rad_create(torch.cuda.current_stream())
+    na, nap = rad.rad_init_angles(ctx, wa["level"])
+    rad.rad_set_metric(ctx, wa["kind"], wa["spin"], wa["ndim"], wa["xf"], wa["bc"])
+    dta = rad.rad_cfl_dt(ctx, wa["cfl"])
+    sha = (wa["n"][2], wa["n"][1], wa["n"][0])
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    gA = {k: t(wa[k]) for k in ("rho", "u", "alpha_a", "alpha_s", "eta", "T")}
+    oa = rad.rad_opts_default(precision=rad.RAD_F64, coupling=rad.RAD_COUPLE_EMISSIVITY)
+    Ia = torch.full(sha + (nap,), 1.0 / (4 * math.pi), dtype=torch.float64, device=dev)
+    Ia[..., na:] = 0
+    lam = torch.ones_like(Ia)
+    lam_n = torch.empty_like(Ia)
+    ga, gs, ge = (torch.zeros(sha, dtype=torch.float64, device=dev) for _ in range(3))
+    Iw = Ia.clone()
+    fwd = _time_steps(lambda: rad.rad_step(ctx, Iw, gA, dta, oa), 8, 2)
+    adj = _time_steps(lambda: rad.rad_step_adjoint(ctx, Ia, gA, dta, oa, lam, lam_n, ga, gs, ge), 8, 2)
+    rad.rad_check(ctx)
+    rad.rad_destroy(ctx)
+    out["adjoint_over_forward"] = {"ratio": adj / fwd, "fwd_ms_per_step": fwd, "adj_ms_per_step": adj,
+                                   "workload": "adjoint2d: Kerr-Schild a=0.5, 256x128, level 4 (162 bins), FP64, "
+                                               "fixed-emissivity coupling; adjoint includes the recomputation"}
+    return out
 
 
 def run_e2e(args, rad, ctx, dt, opts, prec, mom, sh, na, nap, tdt, dev, world):

@@ -136,6 +136,14 @@ typedef struct {
   int zero_guard;    /* apply the guard (default 1) */
   double a_rad;      /* radiation constant, default 1 */
   double gamma;      /* adiabatic index, default 5/3 */
+  double tau_const;  /* C of the optical-depth weighting of the spatial fluxes
+                        (Sec. 2.4): tau = C alpha_E dt / u^0hat at each face,
+                        f = -expm1(-tau^2), upwind state times (1 - g_up + g)
+                        with g_L/R = -f (1 + 1/n^0bar_L/R) and g their face
+                        average; u and alpha_E = alpha_a + alpha_s are face
+                        averages of the two cells.  0 (default) is the
+                        free-streaming flux.  > 0 needs gas u, alpha_a and
+                        alpha_s; rad_step_adjoint requires 0. */
 } rad_opts;
 
 /* Fill *opts with the defaults above (FP64, PLM, thermal coupling). */
@@ -156,6 +164,9 @@ int rad_cfl_dt(rad_ctx *ctx, double cfl, double *dt_out);
  * gas_src (device [k][j][i][4], nullable) receives -(dR^1/2 + dR^2), the
  * RK-weighted change of R^0_mu from the two couplings (the gas's share).
  * Allocates its stage scratch (one intensity array) on first use.
+ * Geodesic levels up to 9 (812 bins: one CTA of at most 512 threads holds
+ * every bin of a cell) and fewer than 2^32 intensity elements per block;
+ * RAD_EUNSUPPORTED otherwise.
  */
 int rad_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt,
              const rad_opts *opts, double *gas_src);
@@ -196,8 +207,9 @@ int rad_moments(rad_ctx *ctx, const void *I, int precision, int frame, int metho
  * adjoint lam_np1 = dL/dI_{n+1}, write lam_n = dL/dI_n and ACCUMULATE
  * (+=) dL/dalpha_a, dL/dalpha_s, dL/deta (device FP64 [k][j][i]) through
  * the step rad_step would take from I_n.  opts->coupling must be
- * RAD_COUPLE_EMISSIVITY or RAD_COUPLE_NONE (T frozen).  lam arrays use the
- * intensity layout and precision.  g_eta may be NULL.
+ * RAD_COUPLE_EMISSIVITY or RAD_COUPLE_NONE (T frozen), and opts->tau_const
+ * must be 0 (RAD_EUNSUPPORTED otherwise).  lam arrays use the intensity
+ * layout and precision.  g_eta may be NULL.
  */
 int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
                      const rad_opts *opts, const void *lam_np1, void *lam_n,

@@ -12,7 +12,9 @@ Readings (the paper names the stage tasks but not the integrator):
   * the n0crit guard of Sec. 2.4 zeroes I where |n_0| < n0crit after the
     coupling of every stage, and bins under the guard convert U -> I as 0;
   * the gas source over the step is -(1/2 dR^1 + dR^2), the RK-weighted
-    change of R^0_mu produced by the two couplings.
+    change of R^0_mu produced by the two couplings;
+  * the optical-depth flux weighting (Sec. 2.4) uses the step's dt in both
+    stages (the stage operator L is the same function of I in both).
 """
 from dataclasses import dataclass
 
@@ -31,12 +33,13 @@ class Opts:
     a_rad: float = 1.0
     gamma: float = 5.0 / 3.0
     couple: bool = True
+    tau_const: float = 0.0      # C of the optical-depth flux weighting (0: free streaming)
 
 
-def operator_L(I, setup, opts):
+def operator_L(I, setup, opts, tau=None):
     """L(I) = -(div_space + div_angle), Eq. radiation_integral without sources."""
     Ie = TR.fill_ghosts(I, setup.grid, setup.ang.perm_pi2)
-    divS = TR.spatial_divergence(Ie, setup, opts.recon)
+    divS = TR.spatial_divergence(Ie, setup, opts.recon, tau)
     divA = TR.angular_divergence(I, setup)
     return -(divS + divA)
 
@@ -56,9 +59,11 @@ def rk2_step(I0, T0, gas, dt, setup, opts):
     """One full step.  Returns (I2, T2, src [.., 4], ok)."""
     f = setup.f
     mask = guard_mask(setup, opts)
+    # optical-depth flux weights: frozen gas, the step's dt in both stages
+    tau = TR.tau_weights(setup, gas, dt, opts.tau_const) if opts.tau_const > 0.0 else None
     U0 = f * I0
     # stage 1
-    U1s = U0 + dt * operator_L(I0, setup, opts)
+    U1s = U0 + dt * operator_L(I0, setup, opts, tau)
     I1s = to_primitive(U1s, setup, mask)
     if opts.couple:
         I1, T1, dR1, ok1 = C.couple(I1s, T0, gas, dt, setup, opts.a_rad, opts.gamma, opts.mode)
@@ -66,7 +71,7 @@ def rk2_step(I0, T0, gas, dt, setup, opts):
         I1, T1, dR1, ok1 = I1s, T0, torch.zeros(T0.shape + (4,), dtype=I0.dtype), torch.ones_like(T0, dtype=torch.bool)
     I1 = torch.where(mask, torch.zeros_like(I1), I1)
     # stage 2
-    U2s = 0.5 * U0 + 0.5 * (f * I1 + dt * operator_L(I1, setup, opts))
+    U2s = 0.5 * U0 + 0.5 * (f * I1 + dt * operator_L(I1, setup, opts, tau))
     I2s = to_primitive(U2s, setup, mask)
     Tm = 0.5 * (T0 + T1)
     if opts.couple:

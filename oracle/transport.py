@@ -3,7 +3,7 @@
 Follows Sec. 2.2 (Eq. radiation_integral: finite-volume / finite-solid-angle
 form), Sec. 2.3 (reconstruction of the primitive I per angle bin, in each
 dimension separately), Sec. 2.4 (Eq. flux_space, Eq. flux_angle: upwind
-fluxes) and Sec. 2.6 (angular fluxes summed over the edges of a geodesic
+fluxes, and the optical-depth weighting of the spatial fluxes) and Sec. 2.6 (angular fluxes summed over the edges of a geodesic
 cell).
 
 Layout: intensities are I[k, j, i, n] (x3, x2, x1, angle), float64.
@@ -219,13 +219,84 @@ def face_states(Ie, grid, d, recon):
     return IL + 0.5 * sL, IR - 0.5 * sR
 
 
-def spatial_divergence(Ie, setup, recon):
-    """(1/dV) sum_d [dA n^d n_0 I_upwind]^+_- (Eq. flux_space, Eq. radiation_integral)."""
+def _gas_ghosts(field, grid):
+    """Gas field [n3, n2, n1, ...] extended by one ghost layer per side in every
+    flux dimension: periodic wrap, outflow copy, polar mirror (the mirrored
+    cell across the pole; polar faces have zero area, so its value never
+    reaches a flux)."""
+    N1, N2, N3 = grid.n
+    ext = field
+    for d in range(grid.ndim):
+        ax = 2 - d
+        N = grid.n[d]
+        parts = []
+        for side in (0, 1):
+            kind = grid.bc[d][side]
+            if kind == "periodic":
+                src = N - 1 if side == 0 else 0
+            else:                       # outflow copy, polar mirror
+                src = 0 if side == 0 else N - 1
+            v = ext.narrow(ax, src, 1)
+            if kind == "polar":
+                v = torch.roll(v, shifts=-(N3 // 2), dims=0)
+            parts.append(v)
+        ext = torch.cat([parts[0], ext, parts[1]], dim=ax)
+    return ext
+
+
+def tau_weights(setup, gas, dt, C):
+    """Optical-depth weighting of the spatial fluxes (Sec. 2.4, after Eq.
+    flux_space).  Per flux dimension, returns the factors (1 - g_L + g,
+    1 - g_R + g) at every face and bin, applied to the left / right upwind
+    state:
+        u^a, alpha_E = alpha_a + alpha_s   averaged to the face from its two cells
+        tau = C alpha_E dt / u^0hat        (u^0hat of the face velocity)
+        f   = -expm1(-tau^2)
+        g_X = -f (1 + 1 / n^0bar_X),  n^0bar_X = u^0hat_X - u_ahat,X n^ahat
+              (X = L, R: the cells on the lesser / greater side)
+        g   = (g_L + g_R) / 2
+    C = 0 gives f = 0 and both factors 1 (the free-streaming flux)."""
+    grid = setup.grid
+    u = gas["u"]
+    aE = gas["alpha_a"] + gas["alpha_s"]
+    ue = _gas_ghosts(u, grid)                       # [.., 3]
+    ae = _gas_ghosts(aE[..., None], grid)[..., 0]
+    out = []
+    for d in range(grid.ndim):
+        ax = 2 - d
+        N = grid.n[d]
+        off = [1 if dd < grid.ndim else 0 for dd in range(3)]      # ghost layers per dimension
+        sl = [slice(off[2], off[2] + grid.n[2]), slice(off[1], off[1] + grid.n[1]),
+              slice(off[0], off[0] + grid.n[0])]
+        sl[ax] = slice(None)
+        uline, aline = ue[tuple(sl)], ae[tuple(sl)]    # cells -1 .. N along ax
+        uL, uR = uline.narrow(ax, 0, N + 1), uline.narrow(ax, 1, N + 1)
+        aL, aR = aline.narrow(ax, 0, N + 1), aline.narrow(ax, 1, N + 1)
+        uF = 0.5 * (uL + uR)
+        aF = 0.5 * (aL + aR)
+        u0F = torch.sqrt(1.0 + (uF * uF).sum(-1))
+        tau = C * aF * dt / u0F
+        f = -torch.expm1(-tau * tau)
+        nbarL = torch.sqrt(1.0 + (uL * uL).sum(-1))[..., None] - uL @ setup.ang.dir.T
+        nbarR = torch.sqrt(1.0 + (uR * uR).sum(-1))[..., None] - uR @ setup.ang.dir.T
+        gL = -f[..., None] * (1.0 + 1.0 / nbarL)
+        gR = -f[..., None] * (1.0 + 1.0 / nbarR)
+        g = 0.5 * (gL + gR)
+        out.append((1.0 - gL + g, 1.0 - gR + g))
+    return out
+
+
+def spatial_divergence(Ie, setup, recon, tau=None):
+    """(1/dV) sum_d [dA n^d n_0 I_upwind]^+_- (Eq. flux_space, Eq. radiation_integral);
+    with tau (from tau_weights) the upwind states carry the optical-depth
+    factors of Sec. 2.4."""
     grid = setup.grid
     div = torch.zeros(grid.shape + (Ie.shape[-1],), dtype=Ie.dtype)
     for d in range(grid.ndim):
         ax = 2 - d
         IL, IR = face_states(Ie, grid, d, recon)
+        if tau is not None:
+            IL, IR = IL * tau[d][0], IR * tau[d][1]
         up = torch.where(setup.fsign[d] < 0.0, IR, IL)     # tie -> left state
         F = setup.fcoef[d] * up
         N = grid.n[d]

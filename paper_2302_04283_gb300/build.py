@@ -13,8 +13,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
 
-SOURCES = ["angles.cpp", "capi.cu", "geom.cu", "step.cu", "moments.cu", "moments_tc.cu", "adjoint.cu",
-           "noalloc.cu"]
+SOURCES = ["angles.cpp", "capi.cu", "geom.cu", "step.cu", "stage_f32_flat.cu", "stage_f32_ang.cu",
+           "stage_f64_flat.cu", "stage_f64_ang.cu", "moments.cu", "moments_tc.cu", "adjoint.cu", "noalloc.cu"]
 
 
 def _compile(src, extra):

@@ -509,6 +509,10 @@ int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
   double *T1 = (double *)(p + 5 * ib), *T2 = (double *)(p + 5 * ib + tb);
   // ---- forward recompute with the pre-coupling primitives kept
   StageArgs s = make_stage_args(ctx, gas, dt, o, nullptr);
+  {
+    const int rc = check_stage(s, f32, err);
+    if (rc != RAD_OK) return rc;
+  }
   s.Iprev = I_n;
   s.I0 = I_n;
   s.Iout = I1;

@@ -79,6 +79,7 @@ void rad_opts_default(rad_opts *o) {
   o->zero_guard = 1;
   o->a_rad = 1.0;
   o->gamma = 5.0 / 3.0;
+  o->tau_const = 0.0;
 }
 
 int rad_init_angles(rad_ctx *ctx, int level, int *n_ang_out, int *n_ang_padded_out) {
@@ -222,6 +223,8 @@ static int check_gas(rad_ctx *ctx, const rad_gas *gas, const rad_opts *o, bool n
     if (o->coupling == RAD_COUPLE_EMISSIVITY && !gas->eta)
       return fail(ctx, RAD_EINVAL, "emissivity coupling needs gas->eta");
   }
+  if (o->tau_const > 0.0 && (!gas->u || !gas->alpha_a || !gas->alpha_s))
+    return fail(ctx, RAD_EINVAL, "the optical-depth flux weighting needs gas u, alpha_a, alpha_s");
   if (need_T && !gas->T) return fail(ctx, RAD_EINVAL, "gas->T is required");
   return RAD_OK;
 }
@@ -233,6 +236,8 @@ static int check_opts(rad_ctx *ctx, const rad_opts *o) {
   if (o->coupling < RAD_COUPLE_THERMAL || o->coupling > RAD_COUPLE_NONE) return fail(ctx, RAD_EINVAL, "bad coupling");
   if (o->coupling == RAD_COUPLE_THERMAL && !(o->gamma > 1.0)) return fail(ctx, RAD_EINVAL, "gamma must be > 1");
   if (!(o->n0crit >= 0.0)) return fail(ctx, RAD_EINVAL, "n0crit must be >= 0");
+  if (!(o->tau_const >= 0.0) || !std::isfinite(o->tau_const))
+    return fail(ctx, RAD_EINVAL, "tau_const must be finite and >= 0");
   return RAD_OK;
 }
 
@@ -245,10 +250,12 @@ int rad_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opt
   if (!I || !aligned16(I)) return fail(ctx, RAD_EINVAL, "I must be a 16-byte aligned device pointer");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, RAD_EINVAL, "dt must be finite and > 0");
   if (ctx->ang.level > rad::kMaxLevelStep)
-    return fail(ctx, RAD_EUNSUPPORTED, "rad_step supports geodesic levels up to 10");
+    return fail(ctx, RAD_EUNSUPPORTED, "rad_step supports geodesic levels up to 9");
   const rad::DevGeom &G = ctx->geom;
   size_t ncell = (size_t)G.n[0] * G.n[1] * G.n[2];
   size_t esz = o->precision == RAD_F32 ? 4 : 8;
+  if (ncell * ctx->ang.n_ap >= ((size_t)1 << 32))
+    return fail(ctx, RAD_EUNSUPPORTED, "rad_step: more than 2^32 intensity elements in one block");
   size_t need = ncell * ctx->ang.n_ap * esz;
   if (ctx->scratch_I_bytes < need) {
     cudaStreamSynchronize(ctx->stream);
@@ -297,10 +304,12 @@ int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double d
   if ((st = check_gas(ctx, gas, o, true)) != RAD_OK) return st;
   if (o->coupling == RAD_COUPLE_THERMAL)
     return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers fixed-emissivity and uncoupled steps");
+  if (o->tau_const != 0.0)
+    return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers the free-streaming flux (tau_const = 0)");
   if (!I_n || !lam_np1 || !lam_n || !g_aa || !g_as) return fail(ctx, RAD_EINVAL, "null argument");
   if (!(dt > 0.0)) return fail(ctx, RAD_EINVAL, "dt must be > 0");
   if (ctx->ang.level > rad::kMaxLevelStep)
-    return fail(ctx, RAD_EUNSUPPORTED, "rad_step_adjoint supports geodesic levels up to 10");
+    return fail(ctx, RAD_EUNSUPPORTED, "rad_step_adjoint supports geodesic levels up to 9");
   std::string err;
   st = rad::launch_adjoint(ctx, I_n, gas, dt, o, lam_np1, lam_n, g_aa, g_as, g_eta, err);
   return st == RAD_OK ? st : fail(ctx, st, err);

@@ -12,7 +12,7 @@
 namespace rad {
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr int kMaxLevelStep = 10;        // rad_step: one CTA holds all bins of a cell (<= 1024)
+constexpr int kMaxLevelStep = 9;         // rad_step: one CTA of <= 512 threads holds all bins of a cell
 constexpr int kMaxSlots = 6;             // neighbours of a geodesic cell
 
 // error bits of the sticky device word (bit k <-> status -k)

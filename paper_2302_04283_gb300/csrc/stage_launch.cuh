@@ -1,0 +1,43 @@
+// Launch of the stage kernel for one precision and geometry class: picks the
+// compile-time variant (PLM or donor cell, stage 1 or 2, with or without the
+// optical-depth flux weighting).  Included by the stage_*.cu translation
+// units only, each of which instantiates one (precision, geometry) pair.
+#pragma once
+
+#include "step_kernel.cuh"
+
+namespace rad {
+
+template <typename R, bool ANG, bool PLM, bool ST2, bool TAU>
+cudaError_t launch_stage_t(const StageArgs &a, int threads, dim3 grid, cudaStream_t st) {
+  size_t smem = stage_smem<R, ANG>(threads, a.nap, a.kc, a.depth, TAU);
+  auto kern = k_stage<R, ANG, PLM, ST2, TAU>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  // the kernel keeps its working set in shared memory: prefer the largest carve-out
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  kern<<<grid, threads + 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R, bool ANG, bool TAU>
+cudaError_t launch_stage_pt(const StageArgs &a, int threads, dim3 grid, cudaStream_t st) {
+  if (a.recon == RAD_RECON_PLM)
+    return a.stage2 ? launch_stage_t<R, ANG, true, true, TAU>(a, threads, grid, st)
+                    : launch_stage_t<R, ANG, true, false, TAU>(a, threads, grid, st);
+  return a.stage2 ? launch_stage_t<R, ANG, false, true, TAU>(a, threads, grid, st)
+                  : launch_stage_t<R, ANG, false, false, TAU>(a, threads, grid, st);
+}
+
+template <typename R, bool ANG>
+cudaError_t launch_stage_rp(const StageArgs &a, cudaStream_t st) {
+  const int threads = (a.nap / 2 + 31) / 32 * 32;     // two bins per consumer thread
+  const int nchunk = (a.n3 + a.kc - 1) / a.kc;
+  const dim3 grid((unsigned)((long long)a.n1 * a.n2 * nchunk));
+  return a.tau_const > 0.0 ? launch_stage_pt<R, ANG, true>(a, threads, grid, st)
+                           : launch_stage_pt<R, ANG, false>(a, threads, grid, st);
+}
+
+}  // namespace rad

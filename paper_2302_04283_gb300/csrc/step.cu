@@ -10,33 +10,6 @@ namespace rad {
 
 namespace {
 
-template <typename R, bool ANG, bool PLM, bool ST2>
-cudaError_t launch_stage_t(const StageArgs &a, int threads, dim3 grid, cudaStream_t st) {
-  size_t smem = stage_smem<R, ANG>(threads, a.nap, a.kc);
-  auto kern = k_stage<R, ANG, PLM, ST2>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  // the kernel keeps its working set in shared memory: prefer the largest carve-out
-  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  kern<<<grid, threads + 32, smem, st>>>(a);
-  return cudaGetLastError();
-}
-
-template <typename R, bool ANG>
-cudaError_t launch_stage_p(const StageArgs &a, cudaStream_t st) {
-  int threads = (a.nap / 2 + 31) / 32 * 32;     // two bins per consumer thread
-  int nchunk = (a.n3 + a.kc - 1) / a.kc;
-  dim3 grid((unsigned)((long long)a.n1 * a.n2 * nchunk));
-  const bool plm = a.recon == RAD_RECON_PLM;
-  if (plm) return a.stage2 ? launch_stage_t<R, ANG, true, true>(a, threads, grid, st)
-                           : launch_stage_t<R, ANG, true, false>(a, threads, grid, st);
-  return a.stage2 ? launch_stage_t<R, ANG, false, true>(a, threads, grid, st)
-                  : launch_stage_t<R, ANG, false, false>(a, threads, grid, st);
-}
-
-
 // dt bound of one (column, bin); atomically reduced as the bit pattern of a
 // positive double (order preserving).
 __global__ void k_cfl(const ColGeo *cols, int n1, int n2, int ndim, const double *xf1, const double *xf2,
@@ -78,8 +51,8 @@ __global__ void k_cfl(const ColGeo *cols, int n1, int n2, int ndim, const double
 }  // namespace
 
 cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st) {
-  if (f32) return ang ? launch_stage_p<float, true>(a, st) : launch_stage_p<float, false>(a, st);
-  return ang ? launch_stage_p<double, true>(a, st) : launch_stage_p<double, false>(a, st);
+  if (f32) return ang ? launch_stage_rp<float, true>(a, st) : launch_stage_rp<float, false>(a, st);
+  return ang ? launch_stage_rp<double, true>(a, st) : launch_stage_rp<double, false>(a, st);
 }
 
 StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src) {
@@ -101,12 +74,26 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
   a.nap = ctx->ang.n_ap;
   a.nang = ctx->ang.n_ang;
   a.ndim = G.ndim;
-  // cells per CTA along x3: up to kMaxChunk, fewer when the chunk's I* does
-  // not fit the shared-memory budget
-  const size_t esz = o->precision == RAD_F32 ? 4 : 8;
-  const long long rows_fit = (long long)(200 * 1024) / ((long long)ctx->ang.n_ap * esz) - kStages * kRows;
-  const int kc_mem = (int)std::max<long long>(1, rows_fit);
-  a.kc = G.ndim >= 3 ? std::min(std::min(G.n[2], kMaxChunk), kc_mem) : 1;
+  // ring depth and cells per CTA along x3: the deepest ring (4, 3, then 2)
+  // that still leaves room for a chunk of min(n3, 8) cells within the
+  // shared-memory budget, then the longest chunk (up to kMaxChunk) that fits
+  {
+    const int threads = (a.nap / 2 + 31) / 32 * 32;
+    const bool f32 = o->precision == RAD_F32;
+    auto smem = [&](int kc, int depth) {
+      return f32 ? stage_smem<float, false>(threads, a.nap, kc, depth, o->tau_const > 0.0)
+                 : stage_smem<double, false>(threads, a.nap, kc, depth, o->tau_const > 0.0);
+    };
+    const size_t budget = (size_t)200 * 1024;
+    const int kmax = G.ndim >= 3 ? std::min(G.n[2], kMaxChunk) : 1;
+    const int kwant = std::min(kmax, 8);
+    int depth = kMaxStages;
+    while (depth > 2 && smem(kwant, depth) > budget) --depth;
+    int kc = kmax;
+    while (kc > 1 && smem(kc, depth) > budget) --kc;
+    a.depth = depth;
+    a.kc = kc;
+  }
   for (int d = 0; d < 3; ++d) {
     a.bc_lo[d] = G.bc_lo[d];
     a.bc_hi[d] = G.bc_hi[d];
@@ -129,8 +116,24 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
   a.n0crit = o->n0crit;
   a.a_rad = o->a_rad;
   a.gamma = o->gamma;
+  a.tau_const = o->tau_const;
   a.err = ctx->err_word;
   return a;
+}
+
+int check_stage(const StageArgs &a, bool f32, std::string &err) {
+  if ((size_t)a.n1 * a.n2 * a.n3 * a.nap >= ((size_t)1 << 32)) {
+    err = "more than 2^32 intensity elements in one block";
+    return RAD_EUNSUPPORTED;
+  }
+  const int threads = (a.nap / 2 + 31) / 32 * 32;
+  const size_t smem = f32 ? stage_smem<float, false>(threads, a.nap, a.kc, a.depth, a.tau_const > 0.0)
+                          : stage_smem<double, false>(threads, a.nap, a.kc, a.depth, a.tau_const > 0.0);
+  if (smem > (size_t)227 * 1024 || threads + 32 > kStageMaxThreads) {
+    err = "the stencil pipeline of this many bins does not fit one CTA in this precision";
+    return RAD_EUNSUPPORTED;
+  }
+  return RAD_OK;
 }
 
 int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src,
@@ -138,17 +141,9 @@ int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_
   StageArgs a = make_stage_args(ctx, gas, dt, o, gas_src);
   const bool f32 = o->precision == RAD_F32;
   const bool ang = ctx->geom.kind != RAD_MINK_CART;
-  if ((size_t)a.n1 * a.n2 * a.n3 * a.nap >= ((size_t)1 << 32)) {
-    err = "rad_step: more than 2^32 intensity elements in one block";
-    return RAD_EUNSUPPORTED;
-  }
   {
-    const int threads = (a.nap / 2 + 31) / 32 * 32;
-    const size_t smem = f32 ? stage_smem<float, false>(threads, a.nap, a.kc) : stage_smem<double, false>(threads, a.nap, a.kc);
-    if (smem > (size_t)227 * 1024) {
-      err = "rad_step: the stencil pipeline of this many bins does not fit shared memory in this precision";
-      return RAD_EUNSUPPORTED;
-    }
+    const int rc = check_stage(a, f32, err);
+    if (rc != RAD_OK) return rc;
   }
   // stage 1: I^0 -> I^1 (scratch), T^0 -> T^1 (scratch)
   a.Iprev = I;

@@ -5,30 +5,43 @@
 // n0crit guard (Sec. 2.4).
 //
 // Work decomposition: one CTA per (i, j) column and chunk of at most
-// kMaxChunk cells along x3; each thread owns two adjacent angle bins (vector
-// loads, packed FP32x2 arithmetic on sm_103a).  The metrics are
-// x3-independent, so every geometric prefactor of a bin is built once per
-// CTA (in the working precision, from the per-column tables) and kept in
-// registers while the thread walks the chunk along x3 with the x3 stencil
-// and its limiter slopes in a sliding register window.  x1 / x2 neighbours
-// are coalesced row loads.
+// kMaxChunk cells along x3.  The metrics are x3-independent, so every
+// geometric prefactor of a bin is built once per CTA (in the working
+// precision, from the per-column tables) and kept in registers while the CTA
+// walks its chunk along x3.  Each consumer thread owns two adjacent angle
+// bins (8- or 16-byte shared-memory accesses, packed FP32x2 arithmetic).
+//
+// Data movement: one extra producer warp streams every cell's stencil rows
+// from global memory into a ring of 2-4 stages in shared memory with 1D bulk
+// TMA copies (cp.async.bulk ... mbarrier::complete_tx).  The rows of a cell
+// are the contiguous x1 block i-2..i+2 (one copy; five at a wrapped or
+// clamped boundary), the four x2 rows j-2, j-1, j+1, j+2, the own column's
+// row at k+2 (the x3 stencil is a sliding register window with its limiter
+// slopes carried along) and, in stage 2, the own row of I^0.  A "full"
+// mbarrier per ring stage counts the bytes in; an "empty" mbarrier per stage
+// collects one arrival per consumer warp before the producer refills it, so
+// no CTA-wide barrier is taken per cell.  Every wait is bounded and sets an
+// error bit on timeout.
 // Boundary conditions are applied by index mapping (no ghost cells):
 // periodic wrap, outflow clamp, and the polar map (theta -> -theta,
 // phi -> phi + pi, bin n -> perm[n]).
 //
-// Three phases per CTA:
-//   A  for each cell: fluxes, stage combination, primitive I* (written to the
-//      output row), and the three angle sums of the coupling (A1 - Ebar, A2,
-//      Ebar; a warp reduce-scatter, per-warp partials in shared memory);
+// Phases per CTA:
+//   A  for each cell: fluxes, stage combination, primitive I* (kept in shared
+//      memory for the chunk), and the three angle sums of the coupling
+//      (A1 - Ebar, A2, Ebar; a warp reduce-scatter, per-warp partials in
+//      shared memory);
 //   B  one thread per cell sums the warp partials and solves its quartic for
 //      T+ in FP64 (all cells of the chunk in parallel);
-//   C  for each cell: the implicit update of every bin from I* (re-read from
-//      the output row, still in L2) and the source S of phase B, and the four
-//      sums of (I+ - I*) n^A dOmega that give the gas source;
+//   C  for each cell: the implicit update of every bin from I* and the source
+//      S of phase B, written to the output row, and the four sums of
+//      (I+ - I*) n^A dOmega that give the gas source;
 //   D  one thread per cell turns those sums into -dR^0_mu.
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <string>
 
 #include "rad_internal.h"
 
@@ -51,6 +64,7 @@ struct StageArgs {
   int stage2;             // 0: U* = U^0 + dt L;  1: U* = U^0/2 + (U^1 + dt L)/2
   double dt, dts;         // full step and coupling step (dt, then dt/2)
   int n1, n2, n3, nap, nang, ndim, kc;
+  int depth;                       // stages of the shared-memory ring (2..kMaxStages)
   int bc_lo[3], bc_hi[3];
   const void *cols;       // ColGeo or ColGeoF
   const void *f1, *f2, *f3;
@@ -58,17 +72,27 @@ struct StageArgs {
   const int *perm, *slot_nbr, *slot_edge, *edge_pq;
   int recon, mode, zero_guard;
   double n0crit, a_rad, gamma;
+  double tau_const;       // C of the optical-depth flux weighting (0: free streaming)
   int *err;
 };
 
 StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src);
 cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st);
+// One precision / geometry class of stage launches (explicitly instantiated in
+// stage_<precision>_<flat|ang>.cu, one translation unit each).
+template <typename R, bool ANG>
+cudaError_t launch_stage_rp(const StageArgs &a, cudaStream_t st);
+// RAD_OK, or RAD_EUNSUPPORTED with a message when a stage launch of this
+// grid / bin count cannot be formed (element count, shared memory, threads).
+int check_stage(const StageArgs &a, bool f32, std::string &err);
 
 template <typename R> struct GeoTypes;
 template <> struct GeoTypes<double> { using Col = ColGeo; using Face = FaceGeo; };
 template <> struct GeoTypes<float> { using Col = ColGeoF; using Face = FaceGeoF; };
 
 template <typename R> __device__ __forceinline__ R fdiv(R a, R b) { return a / b; }
+__device__ __forceinline__ double rexpm1(double x) { return expm1(x); }
+__device__ __forceinline__ float rexpm1(float x) { return expm1f(x); }
 template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
 
 // PLM half-slope q = dl dr / (dl + dr) if dl dr > 0 else 0 (van Leer 1974).
@@ -237,12 +261,31 @@ __device__ __forceinline__ typename P2<R>::V face_div(unsigned um, unsigned up, 
   return P::sub(P::mul(cp, hi), P::mul(cm, lo));
 }
 
+// face_div with the optical-depth factors of Sec. 2.4: at a face with cells
+// L | R the upwind state is multiplied by 1 - g_L + g = 1 + d (from L) or
+// 1 - g_R + g = 1 - d (from R), d = f (1/n^0bar_L - 1/n^0bar_R) / 2; dlo and
+// dhi are d of the lower (m1 | c) and upper (c | p1) faces.
+template <typename R>
+__device__ __forceinline__ typename P2<R>::V face_div_tau(unsigned um, unsigned up, typename P2<R>::V cm,
+                                                        typename P2<R>::V cp, typename P2<R>::V m1,
+                                                        typename P2<R>::V c, typename P2<R>::V p1,
+                                                        typename P2<R>::V qm, typename P2<R>::V qc,
+                                                        typename P2<R>::V qp, typename P2<R>::V dlo,
+                                                        typename P2<R>::V dhi) {
+  using P = P2<R>;
+  const bool umx = um & 1, umy = um & 2, upx = up & 1, upy = up & 2;
+  const auto one = P::mk(R(1), R(1));
+  auto loR = P::mul(P::sub(c, qc), P::sub(one, dlo)), loL = P::mul(P::add(m1, qm), P::add(one, dlo));
+  auto hiR = P::mul(P::sub(p1, qp), P::sub(one, dhi)), hiL = P::mul(P::add(c, qc), P::add(one, dhi));
+  return P::sub(P::mul(cp, sel2<R>(upx, upy, hiR, hiL)), P::mul(cm, sel2<R>(umx, umy, loR, loL)));
+}
+
 // ---------------------------------------------------------------- TMA
 // One-dimensional bulk copies (the TMA engine) global -> shared, completing
 // on an mbarrier with a transaction count.  Rows are n_ap elements, a
 // multiple of 16 bytes, and start on 16-byte boundaries.
-constexpr int kStages = 4;          // ring depth of the stencil pipeline
-constexpr int kStageMaxThreads = 512 + 32;   // consumers (two bins each) + one producer warp
+constexpr int kMaxStages = 4;       // deepest ring of the stencil pipeline (the launcher picks 2..4)
+constexpr int kStageMaxThreads = 512;   // consumers (two bins each) + one producer warp
 constexpr int kRows = 11;           // rows per stage (see k_stage)
 constexpr long long kSpinLimit = 1ll << 28;
 
@@ -276,17 +319,18 @@ __device__ __forceinline__ bool mbar_wait_parity(uint64_t *bar, uint32_t parity)
 
 // Shared-memory footprint (bytes) of k_stage.
 template <typename R, bool ANG>
-__host__ __device__ constexpr size_t stage_smem(int threads, int nap, int kc) {
-  return (size_t)kStages * kRows * nap * sizeof(R)              // staged stencil rows
+__host__ __device__ constexpr size_t stage_smem(int threads, int nap, int kc, int depth, bool tau) {
+  return (size_t)depth * kRows * nap * sizeof(R)                // staged stencil rows
          + (size_t)kc * nap * sizeof(R)                         // I* of the chunk
          + (size_t)kc * 5 * sizeof(R)                           // gas ux uy uz alphaE u0
          + (size_t)kc * (threads / 32) * kNRedC * sizeof(R)     // per-warp partial sums
          + (size_t)kc * kNRedC * sizeof(R)                      // cell sums
          + (size_t)kc * sizeof(R)                               // S per cell
-         + (size_t)2 * kStages * 8 + 16;                        // full and empty mbarriers
+         + (tau ? (size_t)kc * 6 * 5 * sizeof(R) : 0)           // optical-depth data of the six faces
+         + (size_t)2 * kMaxStages * 8 + 16;                     // full and empty mbarriers
 }
 
-template <typename R, bool ANG, bool PLM, bool ST2>
+template <typename R, bool ANG, bool PLM, bool ST2, bool TAU>
 __global__ void __launch_bounds__(kStageMaxThreads) k_stage(StageArgs a) {
   using Col = typename GeoTypes<R>::Col;
   using Face = typename GeoTypes<R>::Face;
@@ -316,24 +360,62 @@ __global__ void __launch_bounds__(kStageMaxThreads) k_stage(StageArgs a) {
   const bool couple = a.mode != RAD_COUPLE_NONE;
 
   // shared memory: staged rows, I* of the chunk, then small per-cell arrays
-  R *stg = (R *)smem_raw;                                  // [kStages][kRows][nap]
-  R *sI = stg + kStages * kRows * a.nap;                   // [kc][nap]
+  R *stg = (R *)smem_raw;                                  // [depth][kRows][nap]
+  R *sI = stg + a.depth * kRows * a.nap;                   // [kc][nap]
   R *sgas = sI + a.kc * a.nap;                             // [kc][5]
   R *red = sgas + a.kc * 5;                                // [kc][nwarp][kNRedC]
   R *sums = red + a.kc * nwarp * kNRedC;                   // [kc][kNRedC]
   R *Sc = sums + a.kc * kNRedC;                            // [kc]
-  uint64_t *bars = (uint64_t *)(((uintptr_t)(Sc + a.kc) + 15) & ~(uintptr_t)15);   // [kStages] full
-  uint64_t *ebars = bars + kStages;                                                   // [kStages] empty
+  constexpr bool tau = TAU;                                // optical-depth flux weighting (Sec. 2.4)
+  R *stau = Sc + a.kc;                                     // [kc][6 faces][f, u^1, u^2, u^3, u^0 of the neighbour]
+  uint64_t *bars = (uint64_t *)(((uintptr_t)(stau + (tau ? a.kc * 30 : 0)) + 15) & ~(uintptr_t)15);   // [depth] full
+  uint64_t *ebars = bars + kMaxStages;                                                // [depth] empty
 
   for (int c = t; c < nc; c += blockDim.x) {
     const unsigned cell = (unsigned)(k0 + c) * ncol + col;
-    if (couple) {
-      const double ux = a.u[3 * cell], uy = a.u[3 * cell + 1], uz = a.u[3 * cell + 2];
-      sgas[5 * c + 0] = (R)ux;
-      sgas[5 * c + 1] = (R)uy;
-      sgas[5 * c + 2] = (R)uz;
-      sgas[5 * c + 3] = (R)(a.aa[cell] + a.as[cell]);
-      sgas[5 * c + 4] = (R)sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+    if (couple || tau) {
+      const R ux = (R)a.u[3 * cell], uy = (R)a.u[3 * cell + 1], uz = (R)a.u[3 * cell + 2];
+      sgas[5 * c + 0] = ux;
+      sgas[5 * c + 1] = uy;
+      sgas[5 * c + 2] = uz;
+      sgas[5 * c + 3] = (R)a.aa[cell] + (R)a.as[cell];
+      sgas[5 * c + 4] = sqrt(R(1) + ux * ux + uy * uy + uz * uz);
+    }
+  }
+  if (tau) {
+    // optical-depth weighting (Sec. 2.4): per cell and face, the face's
+    // f = -expm1(-tau^2) with tau = C alpha_E dt / u^0hat from the face
+    // averages of u and alpha_E, and the neighbour's velocity (for its n^0bar)
+    for (int q = t; q < nc * 6; q += blockDim.x) {
+      const int c = q / 6, s = q % 6, d = s >> 1, sg = (s & 1) ? 1 : -1;
+      R *o = stau + (c * 6 + s) * 5;
+      if (d >= a.ndim) {
+        o[0] = R(0);
+        o[1] = o[2] = o[3] = R(0);
+        o[4] = R(1);
+        continue;
+      }
+      const int k = k0 + c;
+      int ii = i, jj = j, kk = k, pol = 0;
+      if (d == 0) ii = wrap_idx(i + sg, a.n1, a.bc_lo[0], a.bc_hi[0], pol);
+      if (d == 1) {
+        jj = wrap_idx(j + sg, a.n2, a.bc_lo[1], a.bc_hi[1], pol);
+        if (pol && a.n3 > 1) kk = (k + a.n3 / 2) % a.n3;
+      }
+      if (d == 2) kk = wrap_idx(k + sg, a.n3, a.bc_lo[2], a.bc_hi[2], pol);
+      const unsigned cell = (unsigned)k * ncol + col;
+      const unsigned nbc = (unsigned)kk * ncol + (unsigned)jj * a.n1 + ii;
+      const R uxo = (R)a.u[3 * cell], uyo = (R)a.u[3 * cell + 1], uzo = (R)a.u[3 * cell + 2];
+      const R uxn = (R)a.u[3 * nbc], uyn = (R)a.u[3 * nbc + 1], uzn = (R)a.u[3 * nbc + 2];
+      const R aEo = (R)a.aa[cell] + (R)a.as[cell], aEn = (R)a.aa[nbc] + (R)a.as[nbc];
+      const R fx = R(0.5) * (uxo + uxn), fy = R(0.5) * (uyo + uyn), fz = R(0.5) * (uzo + uzn);
+      const R u0F = sqrt(R(1) + fx * fx + fy * fy + fz * fz);
+      const R tq = (R)a.tau_const * (R(0.5) * (aEo + aEn)) * (R)a.dt / u0F;
+      o[0] = -rexpm1(-tq * tq);
+      o[1] = uxn;
+      o[2] = uyn;
+      o[3] = uzn;
+      o[4] = sqrt(R(1) + uxn * uxn + uyn * uyn + uzn * uzn);
     }
   }
 
@@ -456,8 +538,7 @@ __global__ void __launch_bounds__(kStageMaxThreads) k_stage(StageArgs a) {
   auto rowp = [&](const R *base, int ii, int jj, int kk) {
     return base + ((size_t)kk * ncol + (size_t)jj * a.n1 + ii) * a.nap;
   };
-  auto produce = [&](int c) {      // thread 0: issue the copies of cell k0 + c
-    const int st = c % kStages;
+  auto produce = [&](int c, int st) {   // issue the copies of cell k0 + c into ring stage st
     const int k = k0 + c;
     R *dst = stg + (size_t)st * kRows * a.nap;
     uint32_t bytes = (uint32_t)(5 * rowb) + (a.ndim >= 2 ? (uint32_t)(4 * rowb) : 0u) +
@@ -486,7 +567,7 @@ __global__ void __launch_bounds__(kStageMaxThreads) k_stage(StageArgs a) {
   const R c2pre = dts / R(kFourPi);
   const V zero = P::mk(R(0), R(0));
   if (t == 0) {
-    for (int st = 0; st < kStages; ++st) {
+    for (int st = 0; st < a.depth; ++st) {
       mbar_init(&bars[st], 1);
       mbar_init(&ebars[st], (uint32_t)nwarp);
     }
@@ -498,13 +579,18 @@ __global__ void __launch_bounds__(kStageMaxThreads) k_stage(StageArgs a) {
     // ---- producer warp: one lane issues every cell's copies into the ring,
     // waiting for the consumers to release a stage before refilling it
     if (lane == 0) {
+      int st = 0;
+      uint32_t ph = 0;                      // parity of the empty barrier's next phase
       for (int c = 0; c < nc; ++c) {
-        const int st = c % kStages;
-        if (c >= kStages && !mbar_wait_parity(&ebars[st], (uint32_t)(((c / kStages) - 1) & 1))) {
+        if (c >= a.depth && !mbar_wait_parity(&ebars[st], ph)) {
           timeout = true;     // the consumers time out on the full barrier in turn
           break;
         }
-        produce(c);
+        produce(c, st);
+        if (++st == a.depth) {
+          st = 0;
+          if (c >= a.depth) ph ^= 1u;
+        }
       }
     }
   }
@@ -521,17 +607,37 @@ __global__ void __launch_bounds__(kStageMaxThreads) k_stage(StageArgs a) {
       qb = vl2<R>(w1, w2, w3);
     }
   }
+  int st = 0;
+  uint32_t ph = 0;                          // parity of the full barrier's current phase
   for (int c = 0; c < (cons ? nc : 0); ++c) {
-    const int st = c % kStages;
     const R *sr = stg + (size_t)st * kRows * a.nap;
-    if (!mbar_wait_parity(&bars[st], (uint32_t)((c / kStages) & 1))) timeout = true;
+    if (!mbar_wait_parity(&bars[st], ph)) timeout = true;
     V zc, sx = zero;
+    // optical-depth factors d of the six faces (zero without the weighting)
+    V dlo[3] = {zero, zero, zero}, dhi[3] = {zero, zero, zero};
+    if (tau) {
+      const R *g = sgas + 5 * c;
+      const V io = P::rcp(P::sub(P::mk(g[4], g[4]), P::fma(P::mk(g[2], g[2]), nhz,
+                                 P::fma(P::mk(g[1], g[1]), nhy, P::mul(P::mk(g[0], g[0]), nhx)))));
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (d >= a.ndim) break;
+        const R *tl = stau + (c * 6 + 2 * d) * 5, *th = tl + 5;
+        const V im = P::rcp(P::sub(P::mk(tl[4], tl[4]), P::fma(P::mk(tl[3], tl[3]), nhz,
+                                   P::fma(P::mk(tl[2], tl[2]), nhy, P::mul(P::mk(tl[1], tl[1]), nhx)))));
+        const V ip = P::rcp(P::sub(P::mk(th[4], th[4]), P::fma(P::mk(th[3], th[3]), nhz,
+                                   P::fma(P::mk(th[2], th[2]), nhy, P::mul(P::mk(th[1], th[1]), nhx)))));
+        dlo[d] = P::mul(P::mk(R(0.5) * tl[0], R(0.5) * tl[0]), P::sub(im, io));
+        dhi[d] = P::mul(P::mk(R(0.5) * th[0], R(0.5) * th[0]), P::sub(io, ip));
+      }
+    }
     if (d3) {
       const V w4 = sv(sr + 9 * a.nap);
       const V qc = plm ? vl2<R>(w2, w3, w4) : zero;   // slope of k+1
       zc = w2;
       // slopes: qa = slope(k-1), qb = slope(k), qc = slope(k+1)
-      sx = face_div<R>(um[2], up[2], cm[2], cp[2], w1, w2, w3, qa, qb, qc);
+      sx = tau ? face_div_tau<R>(um[2], up[2], cm[2], cp[2], w1, w2, w3, qa, qb, qc, dlo[2], dhi[2])
+               : face_div<R>(um[2], up[2], cm[2], cp[2], w1, w2, w3, qa, qb, qc);
       w0 = w1;
       w1 = w2;
       w2 = w3;
@@ -549,7 +655,8 @@ __global__ void __launch_bounds__(kStageMaxThreads) k_stage(StageArgs a) {
         sc = vl2<R>(m1, zc, q1);
         sp = vl2<R>(zc, q1, q2);
       }
-      sx = P::add(sx, face_div<R>(um[0], up[0], cm[0], cp[0], m1, zc, q1, sm, sc, sp));
+      sx = P::add(sx, tau ? face_div_tau<R>(um[0], up[0], cm[0], cp[0], m1, zc, q1, sm, sc, sp, dlo[0], dhi[0])
+                          : face_div<R>(um[0], up[0], cm[0], cp[0], m1, zc, q1, sm, sc, sp));
     }
     if (a.ndim >= 2) {
       V yv[4];
@@ -564,7 +671,8 @@ __global__ void __launch_bounds__(kStageMaxThreads) k_stage(StageArgs a) {
         sc = vl2<R>(yv[1], zc, yv[2]);
         sp = vl2<R>(zc, yv[2], yv[3]);
       }
-      sx = P::add(sx, face_div<R>(um[1], up[1], cm[1], cp[1], yv[1], zc, yv[2], sm, sc, sp));
+      sx = P::add(sx, tau ? face_div_tau<R>(um[1], up[1], cm[1], cp[1], yv[1], zc, yv[2], sm, sc, sp, dlo[1], dhi[1])
+                          : face_div<R>(um[1], up[1], cm[1], cp[1], yv[1], zc, yv[2], sm, sc, sp));
     }
     V divA = zero;
     if (ANG) {
@@ -608,6 +716,10 @@ __global__ void __launch_bounds__(kStageMaxThreads) k_stage(StageArgs a) {
     if (lane == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&ebars[st])) : "memory");
+    }
+    if (++st == a.depth) {
+      st = 0;
+      ph ^= 1u;
     }
   }
   if (timeout) atomicOr(a.err, 1 << 3);

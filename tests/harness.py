@@ -73,7 +73,7 @@ def oracle_gas(w):
     return g
 
 
-def run_both(w, nsteps, precision="f64", recon="plm", coupling=None, dt=None):
+def run_both(w, nsteps, precision="f64", recon="plm", coupling=None, dt=None, tau=0.0):
     """Advance workload w nsteps on the GPU and in the oracle; return both states."""
     st = oracle_setup(w)
     gc = GpuCase(w)
@@ -82,7 +82,8 @@ def run_both(w, nsteps, precision="f64", recon="plm", coupling=None, dt=None):
     if dt is None:
         dt = OCFL.cfl_dt(st, w["cfl"])
     # oracle
-    opts = OS.Opts(recon=recon, mode=mode if mode != "none" else "thermal", couple=mode != "none")
+    opts = OS.Opts(recon=recon, mode=mode if mode != "none" else "thermal", couple=mode != "none",
+                   tau_const=tau)
     I, T = torch.tensor(w["I0"]), torch.tensor(w["T"])
     gas_o = oracle_gas(w)
     src_tot = torch.zeros(T.shape + (4,), dtype=torch.float64)
@@ -99,7 +100,7 @@ def run_both(w, nsteps, precision="f64", recon="plm", coupling=None, dt=None):
              "none": rad.RAD_COUPLE_NONE}[mode]
     o = rad.rad_opts_default(precision=rad.RAD_F64 if precision == "f64" else rad.RAD_F32,
                              recon=rad.RAD_RECON_PLM if recon == "plm" else rad.RAD_RECON_DC,
-                             coupling=cmode)
+                             coupling=cmode, tau_const=tau)
     for _ in range(nsteps):
         rad.rad_step(gc.ctx, Ig, gas_g, dt, o, src_g)
     rad.rad_check(gc.ctx)

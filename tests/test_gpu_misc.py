@@ -118,6 +118,15 @@ def test_argument_errors_are_reported():
         with pytest.raises(rad.RadError) as e:     # emissivity coupling without eta
             rad.rad_step(ctx, I, gas, 0.1, rad.rad_opts_default(coupling=rad.RAD_COUPLE_EMISSIVITY))
         assert e.value.status == rad.RAD_EINVAL
+        with pytest.raises(rad.RadError) as e:     # negative optical-depth constant
+            rad.rad_step(ctx, I, gas, 0.1, rad.rad_opts_default(tau_const=-1.0))
+        assert e.value.status == rad.RAD_EINVAL
+        lam = torch.zeros_like(I)
+        with pytest.raises(rad.RadError) as e:     # the adjoint covers tau_const = 0 only
+            rad.rad_step_adjoint(ctx, I, gas, 0.01,
+                                 rad.rad_opts_default(coupling=rad.RAD_COUPLE_NONE, tau_const=1.0),
+                                 lam, torch.zeros_like(I), f(1, 4, 4), f(1, 4, 4))
+        assert e.value.status == rad.RAD_EUNSUPPORTED
         rad.rad_step(ctx, I, gas, 0.01, o)         # a valid call on the same context still works
         rad.rad_check(ctx)
     finally:
@@ -125,7 +134,17 @@ def test_argument_errors_are_reported():
 
 
 def test_empty_and_tiny_grids():
-    """One cell with periodic boundaries everywhere: its own neighbour."""
+    """A grid without cells is refused; one cell with periodic boundaries
+    everywhere is its own neighbour."""
+    ctx = rad.rad_create(torch.cuda.current_stream())
+    try:
+        rad.rad_init_angles(ctx, 1)
+        with pytest.raises(rad.RadError) as e:
+            rad.rad_set_metric(ctx, "mink_cart", 0.0, 3, [np.zeros(1), np.linspace(0, 1, 3), np.linspace(0, 1, 3)],
+                               (("periodic", "periodic"),) * 3)
+        assert e.value.status == rad.RAD_EINVAL
+    finally:
+        rad.rad_destroy(ctx)
     w = W.make("turb3d", n=(1, 1, 1), level=1)
     from tests.harness import run_both
     r = run_both(w, 2, "f64")
@@ -159,3 +178,30 @@ def test_moments_split_bf16_tensor_cores(frame, level, n):
         assert (np.abs(got - ref) / scale).max() < 1e-4
     finally:
         gc.close()
+
+
+def test_element_limit_is_refused():
+    """256 x 256 x 261 cells x 252 bins = 4.31e9 > 2^32 elements: refused with
+    RAD_EUNSUPPORTED before any scratch is allocated or kernel launched (the
+    17 GB FP32 intensity buffer itself is allocated, so no access could leave
+    it even without the check)."""
+    n = (256, 256, 261)
+    ctx = rad.rad_create(torch.cuda.current_stream())
+    try:
+        na, nap = rad.rad_init_angles(ctx, 5)
+        xf = [np.linspace(0, 1, m + 1) for m in n]
+        rad.rad_set_metric(ctx, "mink_cart", 0.0, 3, xf, (("periodic", "periodic"),) * 3)
+        assert n[0] * n[1] * n[2] * nap > 2 ** 32
+        I = torch.empty((n[2], n[1], n[0], nap), dtype=torch.float32, device="cuda")
+        sh = (n[2], n[1], n[0])
+        gas = {k: torch.ones(sh, dtype=torch.float64, device="cuda") for k in ("rho", "alpha_a", "alpha_s", "T")}
+        gas["u"] = torch.zeros(sh + (3,), dtype=torch.float64, device="cuda")
+        gas["eta"] = None
+        o = rad.rad_opts_default(precision=rad.RAD_F32)
+        with pytest.raises(rad.RadError) as e:
+            rad.rad_step(ctx, I, gas, 1e-3, o)
+        assert e.value.status == rad.RAD_EUNSUPPORTED
+        del I
+    finally:
+        rad.rad_destroy(ctx)
+        torch.cuda.empty_cache()

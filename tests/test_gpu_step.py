@@ -27,6 +27,8 @@ CASES = [
     ("torus3d", (6, 8, 6), 3, 1),                 # 92 bins
     ("torus3d_big", (6, 4, 4), 2, 2),             # moving gas + scattering in Kerr-Schild
     ("adjoint2d", (10, 8, 1), 2, 2),              # 2D Kerr-Schild, fixed emissivity
+    ("turb3d", (4, 3, 37), 2, 1),                 # x3 longer than one 32-cell chunk, ragged tail
+    ("torus3d_big", (3, 4, 10), 8, 1),            # 642 bins: FP64 ring two stages deep
 ]
 
 
@@ -46,7 +48,7 @@ def test_step_f64_matches_oracle(name, n, level, steps):
         r["gc"].close()
 
 
-@pytest.mark.parametrize("name,n,level,steps", [CASES[0], CASES[2], CASES[4], CASES[6]])
+@pytest.mark.parametrize("name,n,level,steps", [CASES[0], CASES[2], CASES[4], CASES[6], CASES[8], CASES[9]])
 def test_step_f32_matches_oracle(name, n, level, steps):
     w = W.make(name, n=n, level=level)
     r = run_both(w, steps, "f32")
@@ -77,5 +79,46 @@ def test_uniform_equilibrium_is_fixed_point_on_gpu():
     try:
         assert np.abs(r["I_g"] - w["I0"]).max() < 1e-15
         assert np.abs(r["T_g"] - 1.3).max() < 1e-14
+    finally:
+        r["gc"].close()
+
+
+def test_largest_level_step_f64():
+    """Geodesic level 9 (812 bins, the largest rad_step accepts: 416 consumer
+    threads and the producer warp): the FP64 stencil ring is two stages deep."""
+    w = W.make("torus3d", n=(3, 4, 4), level=9)
+    r = run_both(w, 1, "f64")
+    try:
+        assert rel_err(r["I_g"], r["I_o"]) < TOL64
+        assert rel_err(r["T_g"], r["T_o"]) < TOL64
+    finally:
+        r["gc"].close()
+
+
+TAU_CASES = [
+    # name, sizes, level, precision, recon, C
+    ("turb3d", (7, 5, 6), 2, "f64", "plm", 3.0),       # flat, periodic, moving gas
+    ("turb3d", (7, 5, 6), 2, "f32", "plm", 3.0),
+    ("turb3d", (5, 4, 35), 2, "f64", "dc", 10.0),      # two x3 chunks
+    ("torus3d_big", (6, 6, 4), 2, "f64", "plm", 50.0),  # Kerr-Schild, polar, outflow, moving gas
+    ("adjoint2d", (9, 8, 1), 2, "f64", "plm", 5.0),     # 2D (given a moving gas below)
+]
+
+
+@pytest.mark.parametrize("name,n,level,prec,recon,C", TAU_CASES)
+def test_optical_depth_weighted_flux_matches_oracle(name, n, level, prec, recon, C):
+    """The optical-depth weighting of the spatial fluxes (Sec. 2.4) against
+    the oracle; FP64 1e-12, FP32 2e-5 as for the free-streaming step."""
+    w = W.make(name, n=n, level=level)
+    if not np.any(w["u"]):       # the weighting acts only across velocity differences
+        rng = np.random.default_rng(8)
+        v = rng.uniform(-1, 1, w["u"].shape)
+        v *= 0.3 / np.sqrt((v * v).sum(-1)).max()
+        w["u"] = v / np.sqrt(1 - (v * v).sum(-1))[..., None]
+    r = run_both(w, 1, prec, recon=recon, tau=C)
+    try:
+        tol = TOL64 if prec == "f64" else TOL32
+        assert rel_err(r["I_g"], r["I_o"]) < tol
+        assert rel_err(r["T_g"], r["T_o"]) < tol
     finally:
         r["gc"].close()

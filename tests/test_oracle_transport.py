@@ -157,3 +157,63 @@ def test_hohlraum_converges_in_angle():
     e = [_hohlraum_error(N) for N in (1, 2, 4)]
     assert e[0] > e[1] > e[2]
     assert e[2] < 0.03
+
+
+# ---------------------------------------------- optical-depth flux weighting
+def _tau_case(n=(6, 5, 4), level=2, seed=21, umax=0.4):
+    st = cart_setup(n, level, 3)
+    rng = np.random.default_rng(seed)
+    sh = st.grid.shape
+    v = rng.uniform(-1, 1, sh + (3,))
+    v *= umax / np.sqrt((v * v).sum(-1)).max()
+    gas = {"u": torch.tensor(v / np.sqrt(1 - (v * v).sum(-1))[..., None]),
+           "alpha_a": torch.tensor(10.0 ** rng.uniform(-1, 2, sh)),
+           "alpha_s": torch.tensor(10.0 ** rng.uniform(-1, 2, sh))}
+    I = torch.tensor(rng.uniform(0.5, 1.5, sh + (st.ang.n_ang,)))
+    return st, gas, I
+
+
+def _L_tau(st, gas, I, C, dt=0.01, recon="plm"):
+    tau = TR.tau_weights(st, gas, dt, C)
+    return S.operator_L(I, st, S.Opts(recon=recon), tau)
+
+
+def test_tau_weighting_with_zero_constant_is_free_streaming():
+    """Sec. 2.4: a proportionality constant of 0 reduces to the free-streaming flux."""
+    st, gas, I = _tau_case()
+    assert torch.equal(_L_tau(st, gas, I, 0.0), S.operator_L(I, st, S.Opts()))
+
+
+@pytest.mark.parametrize("uniform", [False, True])
+def test_tau_weighting_is_inactive_for_static_or_uniform_gas(uniform):
+    """With the same velocity on both sides of every face, n^0bar_L = n^0bar_R,
+    so g_L = g_R = g and both factors are exactly 1, whatever the optical depth."""
+    st, gas, I = _tau_case()
+    u = gas["u"]
+    gas["u"] = u[:1, :1, :1].expand_as(u).clone() if uniform else torch.zeros_like(u)
+    L0 = S.operator_L(I, st, S.Opts())
+    assert (_L_tau(st, gas, I, 5.0) - L0).abs().max() <= 1e-14 * L0.abs().max()
+
+
+def test_tau_weighting_conserves_with_periodic_boundaries():
+    """Each face carries one flux (the weights are per face), so sum dV U is
+    still conserved to roundoff, and the weighting does change the fluxes."""
+    st, gas, I = _tau_case()
+    L = _L_tau(st, gas, I, 3.0)
+    assert abs(float((L * st.dV[..., None]).sum())) < 1e-13 * float((I * st.dV[..., None]).sum())
+    assert (L - S.operator_L(I, st, S.Opts())).abs().max() > 1e-3 * L.abs().max()
+
+
+def test_tau_weighting_is_quadratic_in_small_optical_depth():
+    """f = -expm1(-tau^2) = tau^2 (1 + O(tau^2)): for small optical depth the
+    departure of every weight from 1 is quadratic in C (ratio 4 when C
+    doubles), and it is not identically zero for a moving gas."""
+    st, gas, I = _tau_case()
+    w1 = TR.tau_weights(st, gas, 1e-2, 1e-3)     # tau <= 2e-3: O(tau^2) terms below 1e-5
+    w2 = TR.tau_weights(st, gas, 1e-2, 2e-3)
+    for d in range(3):
+        for side in (0, 1):
+            a, b = w1[d][side] - 1.0, w2[d][side] - 1.0
+            big = a.abs() > 1e-2 * a.abs().max()
+            assert float(a.abs().max()) > 1e-10
+            assert float((b[big] / a[big] - 4.0).abs().max()) < 1e-4
