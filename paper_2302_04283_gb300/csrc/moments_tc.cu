@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kTcThreads) k_moments_tc(const float *__restri
   const uint32_t bbytes = (uint32_t)kp * kTcN * 2;
   uint64_t *bar = (uint64_t *)(Bw + 2 * bbytes);
   uint32_t *tslot = (uint32_t *)(bar + 1);
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int t = threadIdx.x, warp = t >> 5;
 
   // W^T hi / lo (prebuilt layout) into shared memory
   const int nvec = (int)(2 * bbytes / 16);
@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(kTcThreads) k_moments_tc(const float *__restri
     const long long cell0 = tile * kTcM;
     for (int k0 = 0; k0 < kp; k0 += kTcKC) {
       // ---- stage the chunk: 1024 segments of 8 bins, 8 per thread
-#pragma unroll 2
+      // fully unrolled: all sixteen 16-byte loads of a thread are in flight together
+#pragma unroll
       for (int it = 0; it < (kTcM * kTcKC / 8) / kTcThreads; ++it) {
         const int s = it * kTcThreads + t;
         const int g = s >> 5, r = (s & 31) >> 2, kq = s & 3;
@@ -313,11 +314,8 @@ int launch_moments_bf16x3(rad_ctx *ctx, const float *I, int frame, const double 
     if (st != RAD_OK) return st;
   }
   const long long ncell = (long long)G.n[0] * G.n[1] * G.n[2];
-  // operands + W^T + barrier, padded so that any descriptor stride stays in the allocation
-  // (a descriptor read with LBO and SBO exchanged reaches at most 44 KB past
-  // an operand start, so 72 KB keeps every access inside the allocation)
+  // operands (hi, lo) + W^T (hi, lo) + barrier and TMEM slot
   size_t smem = 2 * (size_t)kATile + 2 * (size_t)kp * kTcN * 2 + 64;
-  smem = std::max(smem, (size_t)72 * 1024);
   smem = (smem + 1023) / 1024 * 1024;
   if (smem > 200 * 1024) {
     err = "split-bf16 moments: too many bins for shared memory";
@@ -332,7 +330,8 @@ int launch_moments_bf16x3(rad_ctx *ctx, const float *I, int frame, const double 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   long long ntile = (ncell + kTcM - 1) / kTcM;
-  long long blocks = std::min<long long>(ntile, (long long)nsm * 2);
+  // four resident CTAs per SM keep enough loads in flight for HBM
+  long long blocks = std::min<long long>(ntile, (long long)nsm * 4);
   k_moments_tc<<<(unsigned)blocks, kTcThreads, smem, ctx->stream>>>(I, R, ncell, ctx->ang.n_ap, ctx->ang.n_ang, kp,
                                                                      (const uint4 *)ctx->wt_dev, frame, G.colsF,
                                                                      G.n[0] * G.n[1], u, ctx->err_word);

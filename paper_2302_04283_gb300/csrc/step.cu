@@ -74,9 +74,11 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
   a.nap = ctx->ang.n_ap;
   a.nang = ctx->ang.n_ang;
   a.ndim = G.ndim;
-  // ring depth and cells per CTA along x3: the deepest ring (4, 3, then 2)
-  // that still leaves room for a chunk of min(n3, 8) cells within the
-  // shared-memory budget, then the longest chunk (up to kMaxChunk) that fits
+  // ring depth and cells per CTA along x3: a 3-stage ring (2 when the bins
+  // are too many for a chunk of min(n3, 8) cells within the shared-memory
+  // budget), then the longest chunk (up to kMaxChunk) that fits.  Three
+  // stages cover the copy latency and keep the 162-bin FP32 CTA small
+  // enough for five per SM.
   {
     const int threads = (a.nap / 2 + 31) / 32 * 32;
     const bool f32 = o->precision == RAD_F32;
@@ -87,7 +89,7 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
     const size_t budget = (size_t)200 * 1024;
     const int kmax = G.ndim >= 3 ? std::min(G.n[2], kMaxChunk) : 1;
     const int kwant = std::min(kmax, 8);
-    int depth = kMaxStages;
+    int depth = 3;
     while (depth > 2 && smem(kwant, depth) > budget) --depth;
     int kc = kmax;
     while (kc > 1 && smem(kc, depth) > budget) --kc;

@@ -284,7 +284,7 @@ __device__ __forceinline__ typename P2<R>::V face_div_tau(unsigned um, unsigned 
 // One-dimensional bulk copies (the TMA engine) global -> shared, completing
 // on an mbarrier with a transaction count.  Rows are n_ap elements, a
 // multiple of 16 bytes, and start on 16-byte boundaries.
-constexpr int kMaxStages = 4;       // deepest ring of the stencil pipeline (the launcher picks 2..4)
+constexpr int kMaxStages = 4;       // deepest ring of the stencil pipeline (the launcher picks 2 or 3)
 constexpr int kStageMaxThreads = 512;   // consumers (two bins each) + one producer warp
 constexpr int kRows = 11;           // rows per stage (see k_stage)
 constexpr long long kSpinLimit = 1ll << 28;
@@ -331,7 +331,9 @@ __host__ __device__ constexpr size_t stage_smem(int threads, int nap, int kc, in
 }
 
 template <typename R, bool ANG, bool PLM, bool ST2, bool TAU>
-__global__ void __launch_bounds__(kStageMaxThreads) k_stage(StageArgs a) {
+// Register budget: the FP32 kernels are held to 96 registers (the bound of a
+// 544-thread block) so that five 128-thread CTAs fit an SM; FP64 ones get 128.
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_stage(StageArgs a) {
   using Col = typename GeoTypes<R>::Col;
   using Face = typename GeoTypes<R>::Face;
   using P = P2<R>;
