@@ -203,6 +203,35 @@ int rad_moments(rad_ctx *ctx, const void *I, int precision, int frame, int metho
                 const rad_gas *gas, void *R);
 
 /*
+ * Host-resident data (the paper has no counterpart; it takes the fields to
+ * be resident on the device).  One item is one problem on this context's
+ * grid: its intensity and gas state in host memory (same layouts and
+ * precisions as for rad_step; I is not modified), and host buffers for the
+ * results.
+ */
+typedef struct {
+  const void *I;          /* [n3][n2][n1][n_ang_padded], opts->precision */
+  const double *rho, *u, *alpha_a, *alpha_s;
+  const double *eta;      /* only for RAD_COUPLE_EMISSIVITY */
+  double *T;              /* in/out: the gas temperature after the steps */
+  void *R;                /* out: [k][j][i][10] moments (FP64 for RAD_F64, FP32 for RAD_F32) */
+  void *I_out;            /* out, nullable: the intensity after the steps */
+} rad_host_item;
+
+/*
+ * For each of n_items items: copy I and the gas state to the device, take
+ * nsteps rad_step steps (no gas source), contract with rad_moments (frame,
+ * method as there), and copy R, T (and I_out if given) back.  Two device
+ * slots owned by the context alternate; the copies run on a second stream
+ * and overlap the compute of the neighbouring item, which hides them when
+ * the host buffers are pinned.  Synchronous: returns when every result is in
+ * host memory.  Errors as rad_step / rad_moments; a null host array of an
+ * item is RAD_EINVAL and nothing is enqueued.
+ */
+int rad_step_host(rad_ctx *ctx, int n_items, const rad_host_item *items, double dt,
+                  const rad_opts *opts, int nsteps, int frame, int method);
+
+/*
  * Reverse-mode step: given the state I_n (checkpoint, not modified) and the
  * adjoint lam_np1 = dL/dI_{n+1}, write lam_n = dL/dI_n and ACCUMULATE
  * (+=) dL/dalpha_a, dL/dalpha_s, dL/deta (device FP64 [k][j][i]) through

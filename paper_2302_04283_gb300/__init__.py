@@ -48,6 +48,11 @@ class rad_gas(ctypes.Structure):
     _fields_ = [("rho", _vp), ("u", _vp), ("alpha_a", _vp), ("alpha_s", _vp), ("eta", _vp), ("T", _vp)]
 
 
+class rad_host_item(ctypes.Structure):
+    _fields_ = [("I", _vp), ("rho", _vp), ("u", _vp), ("alpha_a", _vp), ("alpha_s", _vp), ("eta", _vp),
+                ("T", _vp), ("R", _vp), ("I_out", _vp)]
+
+
 class rad_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("recon", ctypes.c_int), ("coupling", ctypes.c_int),
                 ("n0crit", ctypes.c_double), ("zero_guard", ctypes.c_int), ("a_rad", ctypes.c_double),
@@ -87,6 +92,8 @@ def lib():
         "rad_step_adjoint": ([_vp, _vp, P(rad_gas), ctypes.c_double, P(rad_opts), _vp, _vp, _vp, _vp, _vp],
                              ctypes.c_int),
         "rad_loss_outer": ([_vp, _vp, ctypes.c_int, _vp, _vp], ctypes.c_int),
+        "rad_step_host": ([_vp, ctypes.c_int, P(rad_host_item), ctypes.c_double, P(rad_opts), ctypes.c_int,
+                           ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "rad_check": ([_vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -188,6 +195,23 @@ def rad_step_noalloc(ctx, I, gas, dt, opts, gas_src=None):
     g = _gas(gas)
     _check(ctx, lib().rad_step_noalloc(ctx, _ptr(I), ctypes.byref(g), float(dt), ctypes.byref(opts),
                                        _ptr(gas_src)))
+
+
+def rad_step_host(ctx, items, dt, opts, nsteps, frame, method):
+    """items: list of dicts of host (CPU, ideally pinned) tensors with keys
+    I, rho, u, alpha_a, alpha_s, eta (or None), T (in/out), R (out) and
+    optionally I_out.  Copies in, steps, takes the moments and copies back,
+    overlapping the copies of one item with the compute of the other."""
+    arr = (rad_host_item * max(1, len(items)))()
+    for n, it in enumerate(items):
+        for k in ("I", "rho", "u", "alpha_a", "alpha_s", "T", "R"):
+            if it[k].is_cuda:
+                raise ValueError("rad_step_host takes host tensors")
+        a = arr[n]
+        for k in ("I", "rho", "u", "alpha_a", "alpha_s", "eta", "T", "R", "I_out"):
+            setattr(a, k, _ptr(it.get(k)))
+    _check(ctx, lib().rad_step_host(ctx, len(items), arr, float(dt), ctypes.byref(opts), int(nsteps), int(frame),
+                                    int(method)))
 
 
 def rad_moments(ctx, I, precision, frame, method, gas, R):

@@ -65,6 +65,15 @@ void rad_destroy(rad_ctx *ctx) {
   cudaFree(ctx->adj_buf);
   cudaFree(ctx->wt_dev);
   cudaFree(ctx->loss_buf);
+  if (ctx->copy_stream) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamDestroy(ctx->copy_stream);
+    for (int s = 0; s < 2; ++s) {
+      cudaEventDestroy(ctx->ev_h2d[s]);
+      cudaEventDestroy(ctx->ev_done[s]);
+    }
+  }
+  cudaFree(ctx->host_slot_buf);
   delete ctx;
 }
 

@@ -115,80 +115,95 @@ __global__ void __launch_bounds__(kTcThreads) k_moments_tc(const float *__restri
   bool failed = false;
 
   const long long ntile = (ncell + kTcM - 1) / kTcM;
-  for (long long tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
-    const long long cell0 = tile * kTcM;
-    for (int k0 = 0; k0 < kp; k0 += kTcKC) {
-      // ---- stage the chunk: 1024 segments of 8 bins, 8 per thread
-      // fully unrolled: all sixteen 16-byte loads of a thread are in flight together
+  constexpr int kSeg = (kTcM * kTcKC / 8) / kTcThreads;   // 8-bin segments per thread and chunk
+  // segment s of a chunk: cell m of the tile, bins kseg * 8 .. + 7 of the chunk
+  auto seg_m = [&](int it) { const int s = it * kTcThreads + t, g = s >> 5; return (g >> 1) * 8 + ((s & 31) >> 2); };
+  auto seg_k = [&](int it) { const int s = it * kTcThreads + t, g = s >> 5; return (g & 1) * 4 + (s & 3); };
+  // global loads of one chunk into registers (zeros outside the grid and the bins)
+  float4 v[2 * kSeg];
+  auto load = [&](long long tile, int k0) {
 #pragma unroll
-      for (int it = 0; it < (kTcM * kTcKC / 8) / kTcThreads; ++it) {
-        const int s = it * kTcThreads + t;
-        const int g = s >> 5, r = (s & 31) >> 2, kq = s & 3;
-        const int m = (g >> 1) * 8 + r, kseg = (g & 1) * 4 + kq;
-        const int k = k0 + kseg * 8;
-        const long long cell = cell0 + m;
-        float x[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) x[e] = 0.0f;
-        if (cell < ncell) {
-          const float *row = I + cell * nap;
-          if (k < nap) {
-            float4 v = *(const float4 *)(row + k);
-            x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-          }
-          if (k + 4 < nap) {
-            float4 v = *(const float4 *)(row + k + 4);
-            x[4] = v.x; x[5] = v.y; x[6] = v.z; x[7] = v.w;
-          }
-#pragma unroll
-          for (int e = 0; e < 8; ++e)
-            if (k + e >= nang) x[e] = 0.0f;
-        }
-        uint32_t h[4], l[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * e]), h1 = __float2bfloat16_rn(x[2 * e + 1]);
-          float r0 = x[2 * e] - __bfloat162float(h0), r1 = x[2 * e + 1] - __bfloat162float(h1);
-          __nv_bfloat162 hh;
-          hh.x = h0;
-          hh.y = h1;
-          memcpy(&h[e], &hh, 4);
-          l[e] = pack_bf16(r0, r1);
-        }
-        const uint32_t off = (uint32_t)(kseg * 16 + (m >> 3)) * 128u + (uint32_t)(m & 7) * 16u;
-        *(uint4 *)(Ah + off) = make_uint4(h[0], h[1], h[2], h[3]);
-        *(uint4 *)(Al + off) = make_uint4(l[0], l[1], l[2], l[3]);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (t == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-        for (int kk = 0; kk < kTcKC / 16; ++kk) {
-          const uint32_t kb = (uint32_t)((k0 / 16 + kk) * 2) * kBLbo;   // 2 core matrices per K step
-          const uint64_t ah = umma_desc(sAh + kk * 2 * kALbo, kALbo, kASbo);
-          const uint64_t al = umma_desc(sAl + kk * 2 * kALbo, kALbo, kASbo);
-          const uint64_t bh = umma_desc(sBh + kb, kBLbo, kBSbo);
-          const uint64_t bl = umma_desc(sBl + kb, kBLbo, kBSbo);
-          const uint32_t first = (k0 == 0 && kk == 0) ? 0u : 1u;
-          mma_bf16(tmem, ah, bh, first);
-          mma_bf16(tmem, ah, bl, 1u);
-          mma_bf16(tmem, al, bh, 1u);
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_addr(bar))
-                     : "memory");
-      }
-      // the MMAs read shared memory asynchronously: wait before restaging
-      const bool ok = mbar_wait(smem_addr(bar), phase);
-      phase ^= 1u;
-      if (__syncthreads_or(!ok)) {   // the decision is uniform across the CTA
-        if (t == 0) atomicOr(err, kTcErrTimeout);
-        failed = true;
-        break;
-      }
+    for (int it = 0; it < kSeg; ++it) {
+      const long long cell = tile * kTcM + seg_m(it);
+      const int k = k0 + seg_k(it) * 8;
+      const float *row = I + cell * nap;
+      v[2 * it] = (cell < ncell && k < nap) ? __ldg((const float4 *)(row + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      v[2 * it + 1] = (cell < ncell && k + 4 < nap) ? __ldg((const float4 *)(row + k + 4))
+                                                    : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (failed) break;
+  };
+  // split into bf16 hi / lo in the K-major core-matrix layout
+  auto convert = [&](int k0) {
+#pragma unroll
+    for (int it = 0; it < kSeg; ++it) {
+      const int m = seg_m(it), kseg = seg_k(it), k = k0 + kseg * 8;
+      float x[8] = {v[2 * it].x, v[2 * it].y, v[2 * it].z, v[2 * it].w,
+                    v[2 * it + 1].x, v[2 * it + 1].y, v[2 * it + 1].z, v[2 * it + 1].w};
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (k + e >= nang) x[e] = 0.0f;                 // padding bins are not data
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * e]), h1 = __float2bfloat16_rn(x[2 * e + 1]);
+        float r0 = x[2 * e] - __bfloat162float(h0), r1 = x[2 * e + 1] - __bfloat162float(h1);
+        __nv_bfloat162 hh;
+        hh.x = h0;
+        hh.y = h1;
+        memcpy(&h[e], &hh, 4);
+        l[e] = pack_bf16(r0, r1);
+      }
+      const uint32_t off = (uint32_t)(kseg * 16 + (m >> 3)) * 128u + (uint32_t)(m & 7) * 16u;
+      *(uint4 *)(Ah + off) = make_uint4(h[0], h[1], h[2], h[3]);
+      *(uint4 *)(Al + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+  };
+
+  // software pipeline over (tile, chunk) units: the loads of the next unit are
+  // in flight while the tensor cores work on the current one
+  long long tile = blockIdx.x;
+  int k0 = 0;
+  if (tile < ntile) load(tile, k0);
+  while (tile < ntile && !failed) {
+    convert(k0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (t == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int kk = 0; kk < kTcKC / 16; ++kk) {
+        const uint32_t kb = (uint32_t)((k0 / 16 + kk) * 2) * kBLbo;   // 2 core matrices per K step
+        const uint64_t ah = umma_desc(sAh + kk * 2 * kALbo, kALbo, kASbo);
+        const uint64_t al = umma_desc(sAl + kk * 2 * kALbo, kALbo, kASbo);
+        const uint64_t bh = umma_desc(sBh + kb, kBLbo, kBSbo);
+        const uint64_t bl = umma_desc(sBl + kb, kBLbo, kBSbo);
+        const uint32_t first = (k0 == 0 && kk == 0) ? 0u : 1u;
+        mma_bf16(tmem, ah, bh, first);
+        mma_bf16(tmem, ah, bl, 1u);
+        mma_bf16(tmem, al, bh, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_addr(bar))
+                   : "memory");
+    }
+    // next unit's loads, then wait for the MMAs (they read shared memory)
+    const long long cur_tile = tile;
+    const int cur_k0 = k0;
+    k0 += kTcKC;
+    if (k0 >= kp) {
+      k0 = 0;
+      tile += gridDim.x;
+    }
+    if (tile < ntile) load(tile, k0);
+    const bool ok = mbar_wait(smem_addr(bar), phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {   // the decision is uniform across the CTA
+      if (t == 0) atomicOr(err, kTcErrTimeout);
+      failed = true;
+      break;
+    }
+    if (cur_k0 + kTcKC < kp) continue;     // the tile has more chunks
+    const long long cell0 = cur_tile * kTcM;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // ---- epilogue: lane m of TMEM holds the 16 sums of cell cell0 + m
     uint32_t r[16];

@@ -118,6 +118,11 @@ struct rad_ctx {
   // per-row partials of the outgoing-flux loss
   double *loss_buf = nullptr;
   int loss_rows = 0;
+  // rad_step_host: two device slots, a copy stream and its events
+  void *host_slot_buf = nullptr;
+  size_t host_slot_bytes = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
 };
 
 namespace rad {

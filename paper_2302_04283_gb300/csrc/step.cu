@@ -118,6 +118,7 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
   a.n0crit = o->n0crit;
   a.a_rad = o->a_rad;
   a.gamma = o->gamma;
+  a.inv_gm1 = 1.0 / (o->gamma - 1.0);
   a.tau_const = o->tau_const;
   a.err = ctx->err_word;
   return a;

@@ -72,6 +72,7 @@ struct StageArgs {
   const int *perm, *slot_nbr, *slot_edge, *edge_pq;
   int recon, mode, zero_guard;
   double n0crit, a_rad, gamma;
+  double inv_gm1;          // 1 / (gamma - 1)
   double tau_const;       // C of the optical-depth flux weighting (0: free streaming)
   int *err;
 };
@@ -116,48 +117,54 @@ __device__ __forceinline__ R face_val(bool upR, bool plm, R a, R b, R c, R d) {
 // Positive root of B4 T^4 + B1 T + B0 (B4 >= 0, B1 > 0, B0 <= 0).  f is
 // convex and increasing for T >= 0, so Newton from the upper bound
 // min(-B0/B1, (-B0/B4)^(1/4)) (the root lies within a factor 2 below it)
-// decreases monotonically onto the root.  FP32 iterations get close
-// cheaply; FP64 iterations finish (the slope may be the FP32 one: Newton
-// with a slope accurate to 1e-7 still gains seven digits per iteration).
+// decreases monotonically onto the root.  The FP32 path gets close in FP32
+// and finishes with FP64 steps (Newton with a slope accurate to 1e-7 still
+// gains seven digits per step), falling back to the FP64 iteration when the
+// FP64 residual is not small; the FP64 path iterates in FP64 throughout.
 __device__ __forceinline__ double quartic_root(double B4, double B1, double B0, bool full64, bool &ok) {
   if (!(B1 > 0.0) || !(B4 >= 0.0) || !(B0 <= 0.0)) {
     ok = false;
     return 0.0;
   }
   if (B0 == 0.0) return 0.0;
-  double T = -B0 / B1;
-  if (B4 == 0.0) return T;
-  T = fmin(T, sqrt(sqrt(-B0 / B4)));
-  if (full64) {
-    for (int it = 0; it < 80; ++it) {
-      double t2 = T * T;
-      double f = fma(fma(B4, t2 * T, B1), T, B0);
-      double fp = fma(4.0 * B4, t2 * T, B1);
-      double Tn = T - f / fp;
-      if (!(Tn < T)) return T;
-      if (T - Tn <= 1e-16 * T) return Tn;
-      T = Tn;
+  if (B4 == 0.0) return -B0 / B1;
+  if (!full64) {
+    // FP32 bracket and Newton iterations, then two FP64 Newton steps with the
+    // FP32 slope; the FP64 residual decides whether the full FP64 solve below
+    // is still needed (it is not, unless the FP32 range was exceeded)
+    const float b4f = (float)B4, b1f = (float)B1, b0f = (float)B0;
+    float tf = fminf(-b0f / b1f, sqrtf(sqrtf(-b0f / b4f)));
+    for (int it = 0; it < 40; ++it) {
+      const float t2 = tf * tf;
+      const float f = fmaf(fmaf(b4f, t2 * tf, b1f), tf, b0f);
+      const float fp = fmaf(4.0f * b4f, t2 * tf, b1f);
+      const float tn = tf - __fdividef(f, fp);
+      if (!(tn < tf) || !(tn > 0.0f)) break;
+      tf = tn;
     }
-    ok = false;
-    return T;
+    double T = (double)tf, f = 0.0;
+    for (int it = 0; it < 2; ++it) {
+      const double t2 = T * T;
+      f = fma(fma(B4, t2 * T, B1), T, B0);
+      const float fp = fmaf(4.0f * b4f, (float)(t2 * T), b1f);
+      T = T - f * (double)(1.0f / fp);
+    }
+    const double t2 = T * T;
+    f = fma(fma(B4, t2 * T, B1), T, B0);
+    if (T > 0.0 && isfinite(T) && fabs(f) <= 1e-9 * -B0) return T;
   }
-  float tf = (float)T, b4f = (float)B4, b1f = (float)B1, b0f = (float)B0;
-  for (int it = 0; it < 40; ++it) {
-    float t2 = tf * tf;
-    float f = fmaf(fmaf(b4f, t2 * tf, b1f), tf, b0f);
-    float fp = fmaf(4.0f * b4f, t2 * tf, b1f);
-    float tn = tf - __fdividef(f, fp);
-    if (!(tn < tf) || !(tn > 0.0f)) break;
-    tf = tn;
+  // FP64: Newton from the upper bound decreases monotonically onto the root
+  double T = fmin(-B0 / B1, sqrt(sqrt(-B0 / B4)));
+  for (int it = 0; it < 80; ++it) {
+    const double t2 = T * T;
+    const double f = fma(fma(B4, t2 * T, B1), T, B0);
+    const double fp = fma(4.0 * B4, t2 * T, B1);
+    const double Tn = T - f / fp;
+    if (!(Tn < T)) return T;
+    if (T - Tn <= 1e-16 * T) return Tn;
+    T = Tn;
   }
-  T = (double)tf;
-  for (int it = 0; it < 3; ++it) {
-    double t2 = T * T;
-    double f = fma(fma(B4, t2 * T, B1), T, B0);
-    float fp = fmaf(4.0f * b4f, (float)(t2 * T), b1f);
-    T = T - f * (double)(1.0f / fp);
-  }
-  if (!(T > 0.0) || !isfinite(T)) ok = false;
+  ok = false;
   return T;
 }
 
@@ -259,6 +266,21 @@ __device__ __forceinline__ typename P2<R>::V face_div(unsigned um, unsigned up, 
   auto lo = P::add(sel2<R>(umx, umy, c, m1), sel2<R>(umx, umy, P::mk(-qc.x, -qc.y), qm));
   auto hi = P::add(sel2<R>(upx, upy, p1, c), sel2<R>(upx, upy, P::mk(-qp.x, -qp.y), qc));
   return P::sub(P::mul(cp, hi), P::mul(cm, lo));
+}
+
+// face_div in weighted form (no selects in the cell loop): ncmL / ncmR are
+// -(lower-face coefficient) where the upwind state is the left / right one
+// and 0 otherwise; cpL / cpR likewise for the upper face.
+template <typename R>
+__device__ __forceinline__ typename P2<R>::V face_div_w(typename P2<R>::V ncmL, typename P2<R>::V ncmR,
+                                                      typename P2<R>::V cpL, typename P2<R>::V cpR,
+                                                      typename P2<R>::V m1, typename P2<R>::V c,
+                                                      typename P2<R>::V p1, typename P2<R>::V qm,
+                                                      typename P2<R>::V qc, typename P2<R>::V qp, bool plm) {
+  using P = P2<R>;
+  if (!plm) return P::fma(ncmR, c, P::fma(ncmL, m1, P::fma(cpR, p1, P::mul(cpL, c))));
+  const auto loL = P::add(m1, qm), loR = P::sub(c, qc), hiL = P::add(c, qc), hiR = P::sub(p1, qp);
+  return P::fma(ncmR, loR, P::fma(ncmL, loL, P::fma(cpR, hiR, P::mul(cpL, hiL))));
 }
 
 // face_div with the optical-depth factors of Sec. 2.4: at a face with cells
@@ -470,6 +492,21 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
       up[2] = um[2];
     }
   }
+  // weighted coefficients for the flat kernels (the curved ones keep the
+  // select form: their registers go to the angular-flux coefficients)
+  V ncmL[3], ncmR[3], cpL[3], cpR[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    ncmR[d] = P::mk((um[d] & 1) ? -cm[d].x : R(0), (um[d] & 2) ? -cm[d].y : R(0));
+    ncmL[d] = P::mk((um[d] & 1) ? R(0) : -cm[d].x, (um[d] & 2) ? R(0) : -cm[d].y);
+    cpR[d] = P::mk((up[d] & 1) ? cp[d].x : R(0), (up[d] & 2) ? cp[d].y : R(0));
+    cpL[d] = P::mk((up[d] & 1) ? R(0) : cp[d].x, (up[d] & 2) ? R(0) : cp[d].y);
+  }
+  auto divd = [&](int d, V m1, V c, V p1, V qm, V qc, V qp, V dl, V dh) -> V {
+    if (tau) return face_div_tau<R>(um[d], up[d], cm[d], cp[d], m1, c, p1, qm, qc, qp, dl, dh);
+    if (ANG) return face_div<R>(um[d], up[d], cm[d], cp[d], m1, c, p1, qm, qc, qp);
+    return face_div_w<R>(ncmL[d], ncmR[d], cpL[d], cpR[d], m1, c, p1, qm, qc, qp, plm);
+  };
   // angular flux of each bin: divA = a_self I + sum_s a_nb[s] I_{m_s}
   R a_self[2] = {R(0), R(0)}, a_nb[2][kMaxSlots];
   int nb_m[2][kMaxSlots];
@@ -638,8 +675,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
       const V qc = plm ? vl2<R>(w2, w3, w4) : zero;   // slope of k+1
       zc = w2;
       // slopes: qa = slope(k-1), qb = slope(k), qc = slope(k+1)
-      sx = tau ? face_div_tau<R>(um[2], up[2], cm[2], cp[2], w1, w2, w3, qa, qb, qc, dlo[2], dhi[2])
-               : face_div<R>(um[2], up[2], cm[2], cp[2], w1, w2, w3, qa, qb, qc);
+      sx = divd(2, w1, w2, w3, qa, qb, qc, dlo[2], dhi[2]);
       w0 = w1;
       w1 = w2;
       w2 = w3;
@@ -657,15 +693,14 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
         sc = vl2<R>(m1, zc, q1);
         sp = vl2<R>(zc, q1, q2);
       }
-      sx = P::add(sx, tau ? face_div_tau<R>(um[0], up[0], cm[0], cp[0], m1, zc, q1, sm, sc, sp, dlo[0], dhi[0])
-                          : face_div<R>(um[0], up[0], cm[0], cp[0], m1, zc, q1, sm, sc, sp));
+      sx = P::add(sx, divd(0, m1, zc, q1, sm, sc, sp, dlo[0], dhi[0]));
     }
     if (a.ndim >= 2) {
       V yv[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const R *row = sr + (5 + q) * a.nap;
-        yv[q] = (anypol && ypol[q]) ? P::mk(row[p0], row[p1]) : sv(row);
+        yv[q] = (ANG && anypol && ypol[q]) ? P::mk(row[p0], row[p1]) : sv(row);
       }
       V sm = zero, sc = zero, sp = zero;
       if (plm) {
@@ -673,8 +708,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
         sc = vl2<R>(yv[1], zc, yv[2]);
         sp = vl2<R>(zc, yv[2], yv[3]);
       }
-      sx = P::add(sx, tau ? face_div_tau<R>(um[1], up[1], cm[1], cp[1], yv[1], zc, yv[2], sm, sc, sp, dlo[1], dhi[1])
-                          : face_div<R>(um[1], up[1], cm[1], cp[1], yv[1], zc, yv[2], sm, sc, sp));
+      sx = P::add(sx, divd(1, yv[1], zc, yv[2], sm, sc, sp, dlo[1], dhi[1]));
     }
     V divA = zero;
     if (ANG) {
@@ -746,7 +780,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
       double S, Tp = Tst;
       bool ok = true;
       if (a.mode == RAD_COUPLE_THERMAL) {
-        const double cv = a.rho[cell] / (a.gamma - 1.0);
+        const double cv = a.rho[cell] * a.inv_gm1;
         const double B4 = A2 * aa * a.a_rad;
         const double B1 = cv * (1.0 - A2 * as);
         const double B0 = D + A2 * as * Em - B1 * Tst;   // A1 - B1 T- - (1 - A2 alpha_s) Ebar-
