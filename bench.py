@@ -136,11 +136,11 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def setup_gpu(prec, dev, n=None):
+def setup_gpu(prec, dev, n=None, name=WORKLOAD):
     import torch
     import paper_2302_04283_gb300 as rad
     import workloads as W
-    w = W.make(WORKLOAD, n=(n, n, n) if n else None, with_intensity=False)
+    w = W.make(name, n=(n, n, n) if n else None, with_intensity=False)
     ctx = rad.rad_create(torch.cuda.current_stream())
     na, nap = rad.rad_init_angles(ctx, w["level"])
     rad.rad_set_metric(ctx, w["kind"], w["spin"], w["ndim"], w["xf"], w["bc"])
@@ -356,6 +356,23 @@ def run_extras(args, dev):
                         "what": "rad_step FP64 + rad_moments FP64 on CUDA cores, same workload, 3 steps"}
     rad.rad_destroy(ctx)
     del I64, I32, Rb
+    # the Kerr-Schild workloads (angular fluxes, polar and outflow boundaries)
+    for name in ("torus3d", "torus3d_big"):
+        rad, w, ctx, na, nap, dt, sh, _, Ik, gk = setup_gpu("f32", dev, None, name)
+        Rk = torch.zeros(sh + (10,), dtype=torch.float32, device=dev)
+
+        def sk():
+            rad.rad_step(ctx, Ik, gk, dt, o32)
+            rad.rad_moments(ctx, Ik, rad.RAD_F32, rad.RAD_FRAME_TETRAD, rad.RAD_MOM_BF16X3, gk, Rk)
+
+        msk = _time_steps(sk, 3, 1)
+        rad.rad_check(ctx)
+        ncell_k = sh[0] * sh[1] * sh[2]
+        out[name + "_f32"] = {"value": ncell_k * na / (msk * 1e-3), "unit": "cell-angle updates/s",
+                              "ms_per_step": msk, "cells": ncell_k, "bins": na,
+                              "what": "rad_step FP32 + split-BF16 moments, 3 steps, Kerr-Schild a=0.9"}
+        rad.rad_destroy(ctx)
+        del Ik, Rk, gk
     # adjoint / forward on the adjoint workload (FP64, fixed emissivity)
     import workloads as W
     wa = W.make("adjoint2d", with_intensity=False)
@@ -375,10 +392,18 @@ def run_extras(args, dev):
     Iw = Ia.clone()
     fwd = _time_steps(lambda: rad.rad_step(ctx, Iw, gA, dta, oa), 8, 2)
     adj = _time_steps(lambda: rad.rad_step_adjoint(ctx, Ia, gA, dta, oa, lam, lam_n, ga, gs, ge), 8, 2)
+    # the same in FP32
+    o32 = rad.rad_opts_default(precision=rad.RAD_F32, coupling=rad.RAD_COUPLE_EMISSIVITY)
+    Ia32, lam32 = Ia.float(), lam.float()
+    lam_n32, Iw32 = torch.empty_like(Ia32), Ia32.clone()
+    fwd32 = _time_steps(lambda: rad.rad_step(ctx, Iw32, gA, dta, o32), 8, 2)
+    adj32 = _time_steps(lambda: rad.rad_step_adjoint(ctx, Ia32, gA, dta, o32, lam32, lam_n32, ga, gs, ge), 8, 2)
     rad.rad_check(ctx)
     rad.rad_destroy(ctx)
     out["adjoint_over_forward"] = {"ratio": adj / fwd, "fwd_ms_per_step": fwd, "adj_ms_per_step": adj,
-                                   "workload": "adjoint2d: Kerr-Schild a=0.5, 256x128, level 4 (162 bins), FP64, "
+                                   "ratio_f32": adj32 / fwd32, "fwd_ms_per_step_f32": fwd32,
+                                   "adj_ms_per_step_f32": adj32,
+                                   "workload": "adjoint2d: Kerr-Schild a=0.5, 256x128, level 4 (162 bins), "
                                                "fixed-emissivity coupling; adjoint includes the recomputation"}
     return out
 

@@ -223,8 +223,8 @@ typedef struct {
  * nsteps rad_step steps (no gas source), contract with rad_moments (frame,
  * method as there), and copy R, T (and I_out if given) back.  Two device
  * slots owned by the context alternate; the copies run on a second stream
- * and overlap the compute of the neighbouring item, which hides them when
- * the host buffers are pinned.  Synchronous: returns when every result is in
+ * and the moment contraction on a third, so that each overlaps the steps of
+ * the neighbouring item (the copies hide when the host buffers are pinned).  Synchronous: returns when every result is in
  * host memory.  Errors as rad_step / rad_moments; a null host array of an
  * item is RAD_EINVAL and nothing is enqueued.
  */

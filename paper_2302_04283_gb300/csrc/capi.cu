@@ -67,9 +67,12 @@ void rad_destroy(rad_ctx *ctx) {
   cudaFree(ctx->loss_buf);
   if (ctx->copy_stream) {
     cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamSynchronize(ctx->mom_stream);
     cudaStreamDestroy(ctx->copy_stream);
+    cudaStreamDestroy(ctx->mom_stream);
     for (int s = 0; s < 2; ++s) {
       cudaEventDestroy(ctx->ev_h2d[s]);
+      cudaEventDestroy(ctx->ev_step[s]);
       cudaEventDestroy(ctx->ev_done[s]);
     }
   }
@@ -300,7 +303,7 @@ int rad_moments(rad_ctx *ctx, const void *I, int precision, int frame, int metho
   if (frame == RAD_FRAME_FLUID && (!gas || !gas->u)) return fail(ctx, RAD_EINVAL, "fluid frame needs gas->u");
   if (!aligned16(I) || !aligned16(R)) return fail(ctx, RAD_EINVAL, "I and R must be 16-byte aligned");
   std::string err;
-  int st = rad::launch_moments(ctx, I, precision, frame, method, gas, R, err);
+  int st = rad::launch_moments(ctx, I, precision, frame, method, gas, R, ctx->stream, err);
   return st == RAD_OK ? st : fail(ctx, st, err);
 }
 

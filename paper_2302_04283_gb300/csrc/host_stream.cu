@@ -10,7 +10,9 @@
 //
 // Order on the copy stream: H2D(0), then for every item i: H2D(i + 1) (after
 // the compute of item i - 1 has released that slot), D2H(i) (after the
-// compute of item i).  The compute stream waits for H2D(i) before item i.
+// compute of item i).  The context stream waits for H2D(i) and runs the steps
+// of item i; a third stream runs its moment contraction, so that the
+// (bandwidth-bound) contraction of one item overlaps the steps of the next.
 #include <cstring>
 
 #include "rad_internal.h"
@@ -39,6 +41,9 @@ extern "C" int rad_step_host(rad_ctx *ctx, int n_items, const rad_host_item *ite
   if (!items) return fail_h(ctx, RAD_EINVAL, "null items");
   const bool f32 = o->precision == RAD_F32;
   if (!f32 && o->precision != RAD_F64) return fail_h(ctx, RAD_EINVAL, "bad precision");
+  if (frame < RAD_FRAME_TETRAD || frame > RAD_FRAME_FLUID) return fail_h(ctx, RAD_EINVAL, "bad frame");
+  if (method != RAD_MOM_SIMT && method != RAD_MOM_BF16X3) return fail_h(ctx, RAD_EINVAL, "bad method");
+  if (method == RAD_MOM_BF16X3 && !f32) return fail_h(ctx, RAD_EINVAL, "the split-bf16 moments read float intensities");
   const bool with_eta = o->coupling == RAD_COUPLE_EMISSIVITY;
   for (int i = 0; i < n_items; ++i) {
     const rad_host_item &it = items[i];
@@ -61,10 +66,12 @@ extern "C" int rad_step_host(rad_ctx *ctx, int n_items, const rad_host_item *ite
     ctx->host_slot_bytes = 2 * per_slot;
   }
   if (!ctx->copy_stream) {
-    if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
-      return fail_h(ctx, RAD_ECUDA, "rad_step_host: copy stream creation failed");
+    if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->mom_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail_h(ctx, RAD_ECUDA, "rad_step_host: stream creation failed");
     for (int s = 0; s < 2; ++s) {
       cudaEventCreateWithFlags(&ctx->ev_h2d[s], cudaEventDisableTiming);
+      cudaEventCreateWithFlags(&ctx->ev_step[s], cudaEventDisableTiming);
       cudaEventCreateWithFlags(&ctx->ev_done[s], cudaEventDisableTiming);
     }
   }
@@ -82,7 +89,7 @@ extern "C" int rad_step_host(rad_ctx *ctx, int n_items, const rad_host_item *ite
     p += up(3 * bC) + up(bC);                    // u, and one spare field
     slot[s].R = p;
   }
-  cudaStream_t cs = ctx->copy_stream, ks = ctx->stream;
+  cudaStream_t cs = ctx->copy_stream, ks = ctx->stream, ms = ctx->mom_stream;
   auto h2d = [&](int i) {
     const rad_host_item &it = items[i];
     Slot &sl = slot[i & 1];
@@ -103,10 +110,11 @@ extern "C" int rad_step_host(rad_ctx *ctx, int n_items, const rad_host_item *ite
     cudaMemcpyAsync(it.T, sl.T, bC, cudaMemcpyDeviceToHost, cs);
     if (it.I_out) cudaMemcpyAsync(it.I_out, sl.I, bI, cudaMemcpyDeviceToHost, cs);
   };
-  // the copy stream must not start before work already queued on the
-  // context stream (an earlier call may still be using the slots)
+  // the copy and moment streams must not start before work already queued on
+  // the context stream (an earlier call may still be using the slots)
   cudaEventRecord(ctx->ev_done[0], ks);
   cudaStreamWaitEvent(cs, ctx->ev_done[0], 0);
+  cudaStreamWaitEvent(ms, ctx->ev_done[0], 0);
   h2d(0);
   int st = RAD_OK;
   for (int i = 0; i < n_items && st == RAD_OK; ++i) {
@@ -124,14 +132,23 @@ extern "C" int rad_step_host(rad_ctx *ctx, int n_items, const rad_host_item *ite
     g.eta = with_eta ? sl.eta : nullptr;
     g.T = sl.T;
     for (int s = 0; s < nsteps && st == RAD_OK; ++s) st = rad_step(ctx, sl.I, &g, dt, o, nullptr);
-    if (st == RAD_OK) st = rad_moments(ctx, sl.I, o->precision, frame, method, &g, sl.R);
-    cudaEventRecord(ctx->ev_done[i & 1], ks);
+    cudaEventRecord(ctx->ev_step[i & 1], ks);
+    cudaStreamWaitEvent(ms, ctx->ev_step[i & 1], 0);
+    if (st == RAD_OK) {
+      std::string err;
+      st = rad::launch_moments(ctx, sl.I, o->precision, frame, method, &g, sl.R, ms, err);
+      if (st != RAD_OK) fail_h(ctx, st, err);
+    }
+    cudaEventRecord(ctx->ev_done[i & 1], ms);
     d2h(i);
   }
   cudaError_t ce = cudaStreamSynchronize(cs);
+  cudaError_t me = cudaStreamSynchronize(ms);
   cudaError_t ke = cudaStreamSynchronize(ks);
-  if (st != RAD_OK) return st;      // rad_step / rad_moments set the message
-  if (ce != cudaSuccess || ke != cudaSuccess)
-    return fail_h(ctx, RAD_ECUDA, std::string("rad_step_host: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ke));
+  if (st != RAD_OK) return st;      // rad_step / the moments set the message
+  if (ce != cudaSuccess || me != cudaSuccess || ke != cudaSuccess) {
+    const cudaError_t e = ce != cudaSuccess ? ce : (me != cudaSuccess ? me : ke);
+    return fail_h(ctx, RAD_ECUDA, std::string("rad_step_host: ") + cudaGetErrorString(e));
+  }
   return RAD_OK;
 }

@@ -100,22 +100,22 @@ __global__ void k_moments_simt(const R *I, R *out, long long ncell, int ncol, in
 }
 
 int launch_moments_bf16x3(rad_ctx *ctx, const float *I, int frame, const double *u, float *R,
-                          std::string &err);
+                          cudaStream_t st, std::string &err);
 
 int launch_moments(rad_ctx *ctx, const void *I, int precision, int frame, int method, const rad_gas *gas,
-                   void *R, std::string &err) {
+                   void *R, cudaStream_t st, std::string &err) {
   const DevGeom &G = ctx->geom;
   long long ncell = (long long)G.n[0] * G.n[1] * G.n[2];
   const double *u = (frame == RAD_FRAME_FLUID) ? gas->u : nullptr;
-  if (method == RAD_MOM_BF16X3) return launch_moments_bf16x3(ctx, (const float *)I, frame, u, (float *)R, err);
+  if (method == RAD_MOM_BF16X3) return launch_moments_bf16x3(ctx, (const float *)I, frame, u, (float *)R, st, err);
   const int wpb = 8;
   unsigned blocks = (unsigned)((ncell + wpb - 1) / wpb);
   if (precision == RAD_F32)
-    k_moments_simt<float><<<blocks, 32 * wpb, 0, ctx->stream>>>(
+    k_moments_simt<float><<<blocks, 32 * wpb, 0, st>>>(
         (const float *)I, (float *)R, ncell, G.n[0] * G.n[1], ctx->ang.n_ap, ctx->ang.n_ang, ctx->dang.dir,
         ctx->dang.dOmega, frame, G.cols, u);
   else
-    k_moments_simt<double><<<blocks, 32 * wpb, 0, ctx->stream>>>(
+    k_moments_simt<double><<<blocks, 32 * wpb, 0, st>>>(
         (const double *)I, (double *)R, ncell, G.n[0] * G.n[1], ctx->ang.n_ap, ctx->ang.n_ang, ctx->dang.dir,
         ctx->dang.dOmega, frame, G.cols, u);
   cudaError_t ce = cudaGetLastError();

@@ -321,7 +321,8 @@ static int build_wt(rad_ctx *ctx, int kp, std::string &err) {
   return RAD_OK;
 }
 
-int launch_moments_bf16x3(rad_ctx *ctx, const float *I, int frame, const double *u, float *R, std::string &err) {
+int launch_moments_bf16x3(rad_ctx *ctx, const float *I, int frame, const double *u, float *R, cudaStream_t st,
+                          std::string &err) {
   const DevGeom &G = ctx->geom;
   const int kp = (ctx->ang.n_ap + kTcKC - 1) / kTcKC * kTcKC;
   if (ctx->wt_dev == nullptr || ctx->wt_kp != kp || ctx->wt_level != ctx->ang.level) {
@@ -347,7 +348,7 @@ int launch_moments_bf16x3(rad_ctx *ctx, const float *I, int frame, const double 
   long long ntile = (ncell + kTcM - 1) / kTcM;
   // four resident CTAs per SM keep enough loads in flight for HBM
   long long blocks = std::min<long long>(ntile, (long long)nsm * 4);
-  k_moments_tc<<<(unsigned)blocks, kTcThreads, smem, ctx->stream>>>(I, R, ncell, ctx->ang.n_ap, ctx->ang.n_ang, kp,
+  k_moments_tc<<<(unsigned)blocks, kTcThreads, smem, st>>>(I, R, ncell, ctx->ang.n_ap, ctx->ang.n_ang, kp,
                                                                      (const uint4 *)ctx->wt_dev, frame, G.colsF,
                                                                      G.n[0] * G.n[1], u, ctx->err_word);
   ce = cudaGetLastError();

@@ -121,8 +121,8 @@ struct rad_ctx {
   // rad_step_host: two device slots, a copy stream and its events
   void *host_slot_buf = nullptr;
   size_t host_slot_bytes = 0;
-  cudaStream_t copy_stream = nullptr;
-  cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr, mom_stream = nullptr;
+  cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_step[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
 };
 
 namespace rad {
@@ -139,7 +139,7 @@ int launch_cfl(rad_ctx *ctx, double cfl, double *dt_out, std::string &err);
 
 // moments.cu
 int launch_moments(rad_ctx *ctx, const void *I, int precision, int frame, int method,
-                   const rad_gas *gas, void *R, std::string &err);
+                   const rad_gas *gas, void *R, cudaStream_t st, std::string &err);
 
 // adjoint.cu
 int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
