@@ -179,3 +179,47 @@ def test_emissivity_mode_linear_solution():
     lhs = (Ip * nb ** 4) * (n0 + nb * aE * 0.2) - n0 * (I * nb ** 4)
     rhs = nb * 0.2 * (0.3 + 0.8 * Ebp[..., None] / (4 * math.pi))
     assert (lhs - rhs).abs().max() < 1e-14
+
+
+def _golden(name):
+    import os
+    vals = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", name)):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = line.split("=")
+            vals[k.strip()] = [float(x) for x in v.split()]
+    return vals
+
+
+def test_static_equilibration_at_the_papers_time_resolutions():
+    """The printed set-up (tests/golden/static_equilibration.txt) at 100, 10
+    and 1 steps per coupling time: every run heads to T_eq without
+    overshooting and conserves gas + radiation energy; finer steps end
+    closer to T_eq after the same time."""
+    g = _golden("static_equilibration.txt")
+    gam, rho, aa = g["gamma"][0], g["rho"][0], g["alpha_a"][0]
+    T0 = g["p_gas0"][0] / rho                    # p = rho T in these units
+    u0, E0 = T0 * rho / (gam - 1.0), g["u_rad0"][0]
+    Teq = brentq(lambda T: T * rho / (gam - 1) + T ** 4 - (u0 + E0), 0.0, 3.0, xtol=1e-15)
+    st = box_setup(n=(1, 1, 1))
+    sh = st.grid.shape
+    t_end = 5.0 / aa
+    gaps = []
+    for per in g["steps_per_coupling_time"]:
+        dt = 1.0 / (aa * per)
+        I = torch.full(sh + (st.ang.n_ang,), E0 / (4 * math.pi), dtype=F64)
+        T = torch.full(sh, T0, dtype=F64)
+        prev = T0
+        for _ in range(int(round(t_end / dt))):
+            I, T, src, ok = S.rk2_step(I, T, gas_fields(sh, aa=aa, rho=rho), dt, st,
+                                       S.Opts(recon="dc", gamma=gam))
+            assert ok.all()
+            Tn = float(T.flatten()[0])
+            assert Teq - 1e-12 <= Tn <= prev + 1e-12          # monotone towards T_eq, no overshoot
+            E = float((I.flatten(0, 2)[0] * st.ang.dOmega).sum())
+            assert abs(E + Tn * rho / (gam - 1) - (u0 + E0)) < 1e-12 * (u0 + E0)
+            prev = Tn
+        gaps.append(prev - Teq)
+    assert gaps[0] < gaps[1] < gaps[2]
+    assert gaps[2] < 0.1 * (T0 - Teq)                          # even one step per coupling time gets close
