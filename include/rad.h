@@ -61,7 +61,7 @@ typedef enum {
 enum { RAD_MINK_CART = 0, RAD_MINK_SPH = 1, RAD_KS_SPH = 2 };
 enum { RAD_BC_PERIODIC = 0, RAD_BC_OUTFLOW = 1, RAD_BC_POLAR = 2 };
 enum { RAD_F64 = 0, RAD_F32 = 1 };
-enum { RAD_RECON_DC = 0, RAD_RECON_PLM = 1 };
+enum { RAD_RECON_DC = 0, RAD_RECON_PLM = 1, RAD_RECON_PPM = 2 };
 enum { RAD_COUPLE_THERMAL = 0, RAD_COUPLE_EMISSIVITY = 1, RAD_COUPLE_NONE = 2 };
 enum { RAD_FRAME_TETRAD = 0, RAD_FRAME_COORD = 1, RAD_FRAME_FLUID = 2 };
 enum { RAD_MOM_SIMT = 0, RAD_MOM_BF16X3 = 1 };
@@ -130,7 +130,9 @@ typedef struct {
   int precision;     /* RAD_F64 or RAD_F32: element type of I and of the
                         per-angle transport / coupling arithmetic; the
                         geometry, the quartic and the temperature are FP64 */
-  int recon;         /* RAD_RECON_DC or RAD_RECON_PLM (van Leer) */
+  int recon;         /* RAD_RECON_DC, RAD_RECON_PLM (van Leer) or RAD_RECON_PPM
+                        (Colella & Woodward; three-cell stencil: polar
+                        boundaries need n[1] >= 3; not in rad_step_adjoint) */
   int coupling;      /* RAD_COUPLE_THERMAL, _EMISSIVITY or _NONE */
   double n0crit;     /* guard threshold on |n_0| (Sec. 2.4), default 0.1 */
   int zero_guard;    /* apply the guard (default 1) */

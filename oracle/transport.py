@@ -17,7 +17,7 @@ import torch
 from . import DTYPE
 from . import geometry as G
 
-NG = 2
+NG = 3          # ghost layers: PPM reaches three cells (DC and PLM use the inner two)
 
 
 class Grid:
@@ -190,6 +190,40 @@ def van_leer(dl, dr):
     return torch.where(pos, 2.0 * prod / den, torch.zeros_like(dl))
 
 
+def ppm_edges(line, ax):
+    """Monotonised parabola edge values (aL, aR) of every cell of a line (the
+    piecewise parabolic method of Colella & Woodward 1984, cited in Sec. 2.3,
+    on a uniform index grid): van Leer / monotonised-central limited slopes,
+    fourth-order interface values from them, then the two monotonicity
+    constraints (flatten at local extrema; pull the far edge in when the
+    parabola would overshoot).  Returns arrays for cells 2 .. L-3 of the line."""
+    L = line.shape[ax]
+
+    def take(lo, hi, x=line):
+        s = [slice(None)] * x.dim()
+        s[ax] = slice(lo, hi)
+        return x[tuple(s)]
+
+    am, a0, ap = take(0, L - 2), take(1, L - 1), take(2, L)          # cells 1 .. L-2
+    dc = 0.5 * (ap - am)
+    dl, dr = a0 - am, ap - a0
+    mag = torch.minimum(dc.abs(), torch.minimum(2.0 * dl.abs(), 2.0 * dr.abs()))
+    slope = torch.where(dl * dr > 0.0, torch.sign(dc) * mag, torch.zeros_like(dc))
+    # interface e between cells e-1 and e, e = 2 .. L-2 (slope index = cell - 1)
+    edge = 0.5 * (take(1, L - 2) + take(2, L - 1)) - (take(1, L - 2, slope) - take(0, L - 3, slope)) / 6.0
+    a = take(2, L - 2)                                                # cells 2 .. L-3
+    aL, aR = take(0, L - 4, edge), take(1, L - 3, edge)
+    flat = (aR - a) * (a - aL) <= 0.0
+    aL, aR = torch.where(flat, a, aL), torch.where(flat, a, aR)
+    dlr = aR - aL
+    six = dlr * (a - 0.5 * (aL + aR))
+    over_l = six > dlr * dlr / 6.0
+    over_r = -dlr * dlr / 6.0 > six
+    aL = torch.where(over_l, 3.0 * a - 2.0 * aR, aL)
+    aR = torch.where(over_r & ~over_l, 3.0 * a - 2.0 * aL, aR)
+    return aL, aR
+
+
 def face_states(Ie, grid, d, recon):
     """Left/right states of I at the n_d + 1 faces along coordinate d (Sec. 2.3)."""
     ax = 2 - d
@@ -208,6 +242,14 @@ def face_states(Ie, grid, d, recon):
     IR = take(NG, NG + N + 1)
     if recon == "dc":
         return IL, IR
+    if recon == "ppm":
+        aL, aR = ppm_edges(line, ax)                    # cells 2 .. N + 2 NG - 3
+        s = [slice(None)] * 4
+        s[ax] = slice(NG - 3, NG - 3 + N + 1)          # right edges of cells NG-1 .. NG+N-1
+        left = aR[tuple(s)]
+        s[ax] = slice(NG - 2, NG - 2 + N + 1)          # left edges of cells NG .. NG+N
+        right = aL[tuple(s)]
+        return left, right
     dL = take(1, NG + N + 1) - take(0, NG + N)          # I_c - I_{c-1}, c = 1..N+NG
     dR = take(2, NG + N + 2) - take(1, NG + N + 1)      # I_{c+1} - I_c
     slope = van_leer(dL, dR)                            # at extended cells 1..N+NG

@@ -244,7 +244,8 @@ static int check_gas(rad_ctx *ctx, const rad_gas *gas, const rad_opts *o, bool n
 static int check_opts(rad_ctx *ctx, const rad_opts *o) {
   if (!o) return fail(ctx, RAD_EINVAL, "null opts");
   if (o->precision != RAD_F64 && o->precision != RAD_F32) return fail(ctx, RAD_EINVAL, "bad precision");
-  if (o->recon != RAD_RECON_DC && o->recon != RAD_RECON_PLM) return fail(ctx, RAD_EINVAL, "bad recon");
+  if (o->recon != RAD_RECON_DC && o->recon != RAD_RECON_PLM && o->recon != RAD_RECON_PPM)
+    return fail(ctx, RAD_EINVAL, "bad recon");
   if (o->coupling < RAD_COUPLE_THERMAL || o->coupling > RAD_COUPLE_NONE) return fail(ctx, RAD_EINVAL, "bad coupling");
   if (o->coupling == RAD_COUPLE_THERMAL && !(o->gamma > 1.0)) return fail(ctx, RAD_EINVAL, "gamma must be > 1");
   if (!(o->n0crit >= 0.0)) return fail(ctx, RAD_EINVAL, "n0crit must be >= 0");
@@ -318,6 +319,8 @@ int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double d
     return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers fixed-emissivity and uncoupled steps");
   if (o->tau_const != 0.0)
     return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers the free-streaming flux (tau_const = 0)");
+  if (o->recon == RAD_RECON_PPM)
+    return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers DC and PLM reconstruction");
   if (!I_n || !lam_np1 || !lam_n || !g_aa || !g_as) return fail(ctx, RAD_EINVAL, "null argument");
   if (!(dt > 0.0)) return fail(ctx, RAD_EINVAL, "dt must be > 0");
   if (ctx->ang.level > rad::kMaxLevelStep)

@@ -1,6 +1,6 @@
 // Launch of the stage kernel for one precision and geometry class: picks the
-// compile-time variant (PLM or donor cell, stage 1 or 2, with or without the
-// optical-depth flux weighting).  Included by the stage_*.cu translation
+// compile-time variant (donor cell, PLM or PPM, stage 1 or 2, with or without
+// the optical-depth flux weighting).  Included by the stage_*.cu translation
 // units only, each of which instantiates one (precision, geometry) pair.
 #pragma once
 
@@ -8,10 +8,10 @@
 
 namespace rad {
 
-template <typename R, bool ANG, bool PLM, bool ST2, bool TAU>
+template <typename R, bool ANG, int RC, bool ST2, bool TAU>
 cudaError_t launch_stage_t(const StageArgs &a, int threads, dim3 grid, cudaStream_t st) {
-  size_t smem = stage_smem<R, ANG>(threads, a.nap, a.kc, a.depth, TAU);
-  auto kern = k_stage<R, ANG, PLM, ST2, TAU>;
+  size_t smem = stage_smem<R, ANG>(threads, a.nap, a.kc, a.depth, TAU, stage_rows(RC));
+  auto kern = k_stage<R, ANG, RC, ST2, TAU>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -24,11 +24,14 @@ cudaError_t launch_stage_t(const StageArgs &a, int threads, dim3 grid, cudaStrea
 
 template <typename R, bool ANG, bool TAU>
 cudaError_t launch_stage_pt(const StageArgs &a, int threads, dim3 grid, cudaStream_t st) {
+  if (a.recon == RAD_RECON_PPM)
+    return a.stage2 ? launch_stage_t<R, ANG, RAD_RECON_PPM, true, TAU>(a, threads, grid, st)
+                    : launch_stage_t<R, ANG, RAD_RECON_PPM, false, TAU>(a, threads, grid, st);
   if (a.recon == RAD_RECON_PLM)
-    return a.stage2 ? launch_stage_t<R, ANG, true, true, TAU>(a, threads, grid, st)
-                    : launch_stage_t<R, ANG, true, false, TAU>(a, threads, grid, st);
-  return a.stage2 ? launch_stage_t<R, ANG, false, true, TAU>(a, threads, grid, st)
-                  : launch_stage_t<R, ANG, false, false, TAU>(a, threads, grid, st);
+    return a.stage2 ? launch_stage_t<R, ANG, RAD_RECON_PLM, true, TAU>(a, threads, grid, st)
+                    : launch_stage_t<R, ANG, RAD_RECON_PLM, false, TAU>(a, threads, grid, st);
+  return a.stage2 ? launch_stage_t<R, ANG, RAD_RECON_DC, true, TAU>(a, threads, grid, st)
+                  : launch_stage_t<R, ANG, RAD_RECON_DC, false, TAU>(a, threads, grid, st);
 }
 
 template <typename R, bool ANG>

@@ -83,8 +83,8 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
     const int threads = (a.nap / 2 + 31) / 32 * 32;
     const bool f32 = o->precision == RAD_F32;
     auto smem = [&](int kc, int depth) {
-      return f32 ? stage_smem<float, false>(threads, a.nap, kc, depth, o->tau_const > 0.0)
-                 : stage_smem<double, false>(threads, a.nap, kc, depth, o->tau_const > 0.0);
+      return f32 ? stage_smem<float, false>(threads, a.nap, kc, depth, o->tau_const > 0.0, stage_rows(o->recon))
+                 : stage_smem<double, false>(threads, a.nap, kc, depth, o->tau_const > 0.0, stage_rows(o->recon));
     };
     const size_t budget = (size_t)200 * 1024;
     const int kmax = G.ndim >= 3 ? std::min(G.n[2], kMaxChunk) : 1;
@@ -125,13 +125,20 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
 }
 
 int check_stage(const StageArgs &a, bool f32, std::string &err) {
+  if (a.recon == RAD_RECON_PPM && a.ndim >= 2 && a.n2 < 3 &&
+      (a.bc_lo[1] == RAD_BC_POLAR || a.bc_hi[1] == RAD_BC_POLAR)) {
+    err = "PPM across a polar boundary needs at least three cells in x2";
+    return RAD_EUNSUPPORTED;
+  }
   if ((size_t)a.n1 * a.n2 * a.n3 * a.nap >= ((size_t)1 << 32)) {
     err = "more than 2^32 intensity elements in one block";
     return RAD_EUNSUPPORTED;
   }
   const int threads = (a.nap / 2 + 31) / 32 * 32;
-  const size_t smem = f32 ? stage_smem<float, false>(threads, a.nap, a.kc, a.depth, a.tau_const > 0.0)
-                          : stage_smem<double, false>(threads, a.nap, a.kc, a.depth, a.tau_const > 0.0);
+  const size_t smem = f32 ? stage_smem<float, false>(threads, a.nap, a.kc, a.depth, a.tau_const > 0.0,
+                                                     stage_rows(a.recon))
+                          : stage_smem<double, false>(threads, a.nap, a.kc, a.depth, a.tau_const > 0.0,
+                                                      stage_rows(a.recon));
   if (smem > (size_t)227 * 1024 || threads + 32 > kStageMaxThreads) {
     err = "the stencil pipeline of this many bins does not fit one CTA in this precision";
     return RAD_EUNSUPPORTED;

@@ -268,6 +268,61 @@ __device__ __forceinline__ typename P2<R>::V face_div(unsigned um, unsigned up, 
   return P::sub(P::mul(cp, hi), P::mul(cm, lo));
 }
 
+// PPM (Colella & Woodward 1984) face states of the two faces of the middle
+// cell of a seven-cell line a[0..6] (a[3] = own), on a uniform index grid:
+// limited slopes (the smallest of the central difference and twice the
+// one-sided ones, zero at extrema), fourth-order interface values from them,
+// and the two monotonicity constraints on every cell's parabola.  Returns the
+// left / right states of the lower face (cells 2 | 3) and the upper face
+// (cells 3 | 4).
+template <typename R>
+__device__ __forceinline__ void ppm_states1(const R (&a)[7], R &loL, R &loR, R &hiL, R &hiR) {
+  R sl[7];
+#pragma unroll
+  for (int m = 1; m <= 5; ++m) {
+    const R dl = a[m] - a[m - 1], dr = a[m + 1] - a[m], dc = R(0.5) * (a[m + 1] - a[m - 1]);
+    const R mag = fmin(fabs(dc), fmin(R(2) * fabs(dl), R(2) * fabs(dr)));
+    sl[m] = dl * dr > R(0) ? copysign(mag, dc) : R(0);
+  }
+  R e[6];                                      // e[m]: interface between cells m and m + 1
+#pragma unroll
+  for (int m = 1; m <= 4; ++m) e[m] = R(0.5) * (a[m] + a[m + 1]) - (sl[m + 1] - sl[m]) * (R(1) / R(6));
+  R aL[5], aR[5];
+#pragma unroll
+  for (int c = 2; c <= 4; ++c) {
+    R l = e[c - 1], r = e[c];
+    const R v = a[c];
+    if ((r - v) * (v - l) <= R(0)) {
+      l = v;
+      r = v;
+    } else {
+      const R dlr = r - l, six = dlr * (v - R(0.5) * (l + r)), q = dlr * dlr * (R(1) / R(6));
+      if (six > q) l = R(3) * v - R(2) * r;
+      else if (-q > six) r = R(3) * v - R(2) * l;
+    }
+    aL[c] = l;
+    aR[c] = r;
+  }
+  loL = aR[2];
+  loR = aL[3];
+  hiL = aR[3];
+  hiR = aL[4];
+}
+
+template <typename R>
+__device__ __forceinline__ void ppm_states(const typename P2<R>::V (&a)[7], typename P2<R>::V &loL,
+                                           typename P2<R>::V &loR, typename P2<R>::V &hiL,
+                                           typename P2<R>::V &hiR) {
+  R ax[7], ay[7];
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    ax[q] = a[q].x;
+    ay[q] = a[q].y;
+  }
+  ppm_states1<R>(ax, loL.x, loR.x, hiL.x, hiR.x);
+  ppm_states1<R>(ay, loL.y, loR.y, hiL.y, hiR.y);
+}
+
 // face_div in weighted form (no selects in the cell loop): ncmL / ncmR are
 // -(lower-face coefficient) where the upwind state is the left / right one
 // and 0 otherwise; cpL / cpR likewise for the upper face.
@@ -308,7 +363,9 @@ __device__ __forceinline__ typename P2<R>::V face_div_tau(unsigned um, unsigned 
 // multiple of 16 bytes, and start on 16-byte boundaries.
 constexpr int kMaxStages = 4;       // deepest ring of the stencil pipeline (the launcher picks 2 or 3)
 constexpr int kStageMaxThreads = 512;   // consumers (two bins each) + one producer warp
-constexpr int kRows = 11;           // rows per stage (see k_stage)
+// rows per ring stage: the x1 block (2h + 1 rows), the 2h x2 rows, the own
+// row at k + h and the own row of I^0, with h = 2 (DC, PLM) or 3 (PPM)
+__host__ __device__ constexpr int stage_rows(int recon) { return recon == RAD_RECON_PPM ? 15 : 11; }
 constexpr long long kSpinLimit = 1ll << 28;
 
 __device__ __forceinline__ uint32_t s_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -341,8 +398,8 @@ __device__ __forceinline__ bool mbar_wait_parity(uint64_t *bar, uint32_t parity)
 
 // Shared-memory footprint (bytes) of k_stage.
 template <typename R, bool ANG>
-__host__ __device__ constexpr size_t stage_smem(int threads, int nap, int kc, int depth, bool tau) {
-  return (size_t)depth * kRows * nap * sizeof(R)                // staged stencil rows
+__host__ __device__ constexpr size_t stage_smem(int threads, int nap, int kc, int depth, bool tau, int rows) {
+  return (size_t)depth * rows * nap * sizeof(R)                 // staged stencil rows
          + (size_t)kc * nap * sizeof(R)                         // I* of the chunk
          + (size_t)kc * 5 * sizeof(R)                           // gas ux uy uz alphaE u0
          + (size_t)kc * (threads / 32) * kNRedC * sizeof(R)     // per-warp partial sums
@@ -352,10 +409,11 @@ __host__ __device__ constexpr size_t stage_smem(int threads, int nap, int kc, in
          + (size_t)2 * kMaxStages * 8 + 16;                     // full and empty mbarriers
 }
 
-template <typename R, bool ANG, bool PLM, bool ST2, bool TAU>
-// Register budget: the FP32 kernels are held to 96 registers (the bound of a
-// 544-thread block) so that five 128-thread CTAs fit an SM; FP64 ones get 128.
-__global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_stage(StageArgs a) {
+template <typename R, bool ANG, int RC, bool ST2, bool TAU>
+// Register budget: the FP32 DC / PLM kernels are held to 96 registers (the
+// bound of a 544-thread block) so that five 128-thread CTAs fit an SM; FP64
+// and PPM ones get 128.
+__global__ void __launch_bounds__((sizeof(R) == 4 && RC != RAD_RECON_PPM) ? 544 : kStageMaxThreads) k_stage(StageArgs a) {
   using Col = typename GeoTypes<R>::Col;
   using Face = typename GeoTypes<R>::Face;
   using P = P2<R>;
@@ -380,12 +438,16 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
   const R *Ip = (const R *)a.Iprev;
   const R *I0 = (const R *)a.I0;
   R *Io = (R *)a.Iout;
-  constexpr bool plm = PLM;
+  constexpr bool plm = RC == RAD_RECON_PLM;
+  constexpr bool ppm = RC == RAD_RECON_PPM;
+  constexpr int H = ppm ? 3 : 2;                           // stencil half-width
+  constexpr int X1N = 2 * H + 1, X2N = 2 * H;              // rows of the x1 block, x2 rows
+  constexpr int SX2 = X1N, SX3 = X1N + X2N, SI0 = SX3 + 1, ROWS = SI0 + 1;   // ring slots
   const bool couple = a.mode != RAD_COUPLE_NONE;
 
   // shared memory: staged rows, I* of the chunk, then small per-cell arrays
-  R *stg = (R *)smem_raw;                                  // [depth][kRows][nap]
-  R *sI = stg + a.depth * kRows * a.nap;                   // [kc][nap]
+  R *stg = (R *)smem_raw;                                  // [depth][ROWS][nap]
+  R *sI = stg + a.depth * ROWS * a.nap;                    // [kc][nap]
   R *sgas = sI + a.kc * a.nap;                             // [kc][5]
   R *red = sgas + a.kc * 5;                                // [kc][nwarp][kNRedC]
   R *sums = red + a.kc * nwarp * kNRedC;                   // [kc][kNRedC]
@@ -465,6 +527,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
   const bool g1 = act1 && a.zero_guard && fabs((double)nlow0.y) < a.n0crit;
   // primitive recovery factor (0 for guarded or inactive bins)
   const V inv_f = P::mk((act0 && !g0) ? R(1) / fconv.x : R(0), (act1 && !g1) ? R(1) / fconv.y : R(0));
+  const V keep = P::mk((act0 && !g0) ? R(1) : R(0), (act1 && !g1) ? R(1) : R(0));   // 0: guarded or padding
   const R invdV = cg.invdV;
   auto fcoef = [&](const Face &F, unsigned &upR) -> V {
     V na = P::fma(nhz, P::mk(F.ea[3], F.ea[3]),
@@ -506,6 +569,21 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
     if (tau) return face_div_tau<R>(um[d], up[d], cm[d], cp[d], m1, c, p1, qm, qc, qp, dl, dh);
     if (ANG) return face_div<R>(um[d], up[d], cm[d], cp[d], m1, c, p1, qm, qc, qp);
     return face_div_w<R>(ncmL[d], ncmR[d], cpL[d], cpR[d], m1, c, p1, qm, qc, qp, plm);
+  };
+  // the same from given face states (loL | loR at the lower face, hiL | hiR at the upper)
+  auto divs = [&](int d, V loL, V loR, V hiL, V hiR, V dl, V dh) -> V {
+    if (tau) {
+      const V one = P::mk(R(1), R(1));
+      loL = P::mul(loL, P::add(one, dl));
+      loR = P::mul(loR, P::sub(one, dl));
+      hiL = P::mul(hiL, P::add(one, dh));
+      hiR = P::mul(hiR, P::sub(one, dh));
+    }
+    if (ANG || tau) {
+      const bool umx = um[d] & 1, umy = um[d] & 2, upx = up[d] & 1, upy = up[d] & 2;
+      return P::sub(P::mul(cp[d], sel2<R>(upx, upy, hiR, hiL)), P::mul(cm[d], sel2<R>(umx, umy, loR, loL)));
+    }
+    return P::fma(ncmR[d], loR, P::fma(ncmL[d], loL, P::fma(cpR[d], hiR, P::mul(cpL[d], hiL))));
   };
   // angular flux of each bin: divA = a_self I + sum_s a_nb[s] I_{m_s}
   R a_self[2] = {R(0), R(0)}, a_nb[2][kMaxSlots];
@@ -549,22 +627,23 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
       a_self[e] = ac ? self / (e ? dO_[1] : dO_[0]) : R(0);
     }
   }
-  // ---- stencil rows of one cell: the contiguous x1 block (rows i-2..i+2, or
-  // one copy per row at a boundary), the four x2 rows, this column's row at
-  // k+2 (x3 window) and, in stage 2, this column's row of I^0.
-  // Slots: 0..4 x1 block (2 = own), 5..8 x2 rows j-2, j-1, j+1, j+2, 9 own k+2, 10 I^0.
-  const int offs[4] = {-2, -1, 1, 2};
-  int xs[5], yj[4], ypol[4];
+  // ---- stencil rows of one cell (h = 2, or 3 for PPM): the contiguous x1
+  // block (rows i-h..i+h, or one copy per row at a boundary), the 2h x2 rows,
+  // this column's row at k+h (x3 window) and, in stage 2, this column's row
+  // of I^0.  Slots: 0..2h x1 block (h = own), then the x2 rows j-h..j+h
+  // without j, then own k+h, then I^0.
+  int xs[X1N], yj[X2N], ypol[X2N];
   bool x1contig = true;
-  for (int q = 0; q < 5; ++q) {
+  for (int q = 0; q < X1N; ++q) {
     int pol;
-    xs[q] = q == 2 ? i : wrap_idx(i + q - 2, a.n1, a.bc_lo[0], a.bc_hi[0], pol);
-    if (xs[q] != i + q - 2) x1contig = false;
+    xs[q] = q == H ? i : wrap_idx(i + q - H, a.n1, a.bc_lo[0], a.bc_hi[0], pol);
+    if (xs[q] != i + q - H) x1contig = false;
   }
   bool anypol = false;
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < X2N; ++q) {
     int pol = 0;
-    yj[q] = a.ndim >= 2 ? wrap_idx(j + offs[q], a.n2, a.bc_lo[1], a.bc_hi[1], pol) : j;
+    const int o = q < H ? q - H : q - H + 1;
+    yj[q] = a.ndim >= 2 ? wrap_idx(j + o, a.n2, a.bc_lo[1], a.bc_hi[1], pol) : j;
     ypol[q] = pol;
     anypol |= pol != 0;
   }
@@ -579,24 +658,24 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
   };
   auto produce = [&](int c, int st) {   // issue the copies of cell k0 + c into ring stage st
     const int k = k0 + c;
-    R *dst = stg + (size_t)st * kRows * a.nap;
-    uint32_t bytes = (uint32_t)(5 * rowb) + (a.ndim >= 2 ? (uint32_t)(4 * rowb) : 0u) +
+    R *dst = stg + (size_t)st * ROWS * a.nap;
+    uint32_t bytes = (uint32_t)(X1N * rowb) + (a.ndim >= 2 ? (uint32_t)(X2N * rowb) : 0u) +
                      (d3 ? (uint32_t)rowb : 0u) + (ST2 ? (uint32_t)rowb : 0u);
     mbar_expect_tx(&bars[st], bytes);
     if (x1contig) {
-      bulk_g2s(dst, rowp(Ip, i - 2, j, k), (uint32_t)(5 * rowb), &bars[st]);
+      bulk_g2s(dst, rowp(Ip, i - H, j, k), (uint32_t)(X1N * rowb), &bars[st]);
     } else {
-      for (int q = 0; q < 5; ++q) bulk_g2s(dst + q * a.nap, rowp(Ip, xs[q], j, k), (uint32_t)rowb, &bars[st]);
+      for (int q = 0; q < X1N; ++q) bulk_g2s(dst + q * a.nap, rowp(Ip, xs[q], j, k), (uint32_t)rowb, &bars[st]);
     }
     if (a.ndim >= 2) {
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < X2N; ++q) {
         int kk = k;
         if (ypol[q] && a.n3 > 1) kk = (k + a.n3 / 2) % a.n3;
-        bulk_g2s(dst + (5 + q) * a.nap, rowp(Ip, i, yj[q], kk), (uint32_t)rowb, &bars[st]);
+        bulk_g2s(dst + (SX2 + q) * a.nap, rowp(Ip, i, yj[q], kk), (uint32_t)rowb, &bars[st]);
       }
     }
-    if (d3) bulk_g2s(dst + 9 * a.nap, rowp(Ip, i, j, kidx(k + 2)), (uint32_t)rowb, &bars[st]);
-    if (ST2) bulk_g2s(dst + 10 * a.nap, rowp(I0, i, j, k), (uint32_t)rowb, &bars[st]);
+    if (d3) bulk_g2s(dst + SX3 * a.nap, rowp(Ip, i, j, kidx(k + H)), (uint32_t)rowb, &bars[st]);
+    if (ST2) bulk_g2s(dst + SI0 * a.nap, rowp(I0, i, j, k), (uint32_t)rowb, &bars[st]);
   };
   const int p0 = act0 ? a.perm[b0] : 0, p1 = act1 ? a.perm[b0 + 1] : 0;
   const unsigned own = (unsigned)col * a.nap + (inpair ? b0 : 0);
@@ -636,7 +715,14 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
 
   // ---- phase A (consumer warps): transport, stage combination, primitive I*, coupling sums
   V w0 = zero, w1 = zero, w2 = zero, w3 = zero, qa = zero, qb = zero;   // x3 window and slopes
-  if (cons && d3) {
+  V pw[6];                                               // PPM x3 window, rows k-3 .. k+2
+#pragma unroll
+  for (int q = 0; q < 6; ++q) pw[q] = zero;
+  if (ppm && cons && d3) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) pw[q] = __ldg((const V *)(Ip + (unsigned)kidx(k0 - 3 + q) * strideK + own));
+  }
+  if (!ppm && cons && d3) {
     w0 = __ldg((const V *)(Ip + (unsigned)kidx(k0 - 2) * strideK + own));
     w1 = __ldg((const V *)(Ip + (unsigned)kidx(k0 - 1) * strideK + own));
     w2 = __ldg((const V *)(Ip + (unsigned)kidx(k0) * strideK + own));
@@ -649,7 +735,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
   int st = 0;
   uint32_t ph = 0;                          // parity of the full barrier's current phase
   for (int c = 0; c < (cons ? nc : 0); ++c) {
-    const R *sr = stg + (size_t)st * kRows * a.nap;
+    const R *sr = stg + (size_t)st * ROWS * a.nap;
     if (!mbar_wait_parity(&bars[st], ph)) timeout = true;
     V zc, sx = zero;
     // optical-depth factors d of the six faces (zero without the weighting)
@@ -670,8 +756,19 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
         dhi[d] = P::mul(P::mk(R(0.5) * th[0], R(0.5) * th[0]), P::sub(io, ip));
       }
     }
-    if (d3) {
-      const V w4 = sv(sr + 9 * a.nap);
+    if (d3 && ppm) {
+      V win[7];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) win[q] = pw[q];
+      win[6] = sv(sr + SX3 * a.nap);
+      zc = win[3];
+      V loL, loR, hiL, hiR;
+      ppm_states<R>(win, loL, loR, hiL, hiR);
+      sx = divs(2, loL, loR, hiL, hiR, dlo[2], dhi[2]);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) pw[q] = win[q + 1];
+    } else if (d3) {
+      const V w4 = sv(sr + SX3 * a.nap);
       const V qc = plm ? vl2<R>(w2, w3, w4) : zero;   // slope of k+1
       zc = w2;
       // slopes: qa = slope(k-1), qb = slope(k), qc = slope(k+1)
@@ -683,9 +780,16 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
       qa = qb;
       qb = qc;
     } else {
-      zc = sv(sr + 2 * a.nap);
+      zc = sv(sr + H * a.nap);
     }
-    {
+    if (ppm) {
+      V v[7];
+#pragma unroll
+      for (int q = 0; q < 7; ++q) v[q] = q == H ? zc : sv(sr + q * a.nap);
+      V loL, loR, hiL, hiR;
+      ppm_states<R>(v, loL, loR, hiL, hiR);
+      sx = P::add(sx, divs(0, loL, loR, hiL, hiR, dlo[0], dhi[0]));
+    } else {
       const V m2 = sv(sr), m1 = sv(sr + a.nap), q1 = sv(sr + 3 * a.nap), q2 = sv(sr + 4 * a.nap);
       V sm = zero, sc = zero, sp = zero;
       if (plm) {
@@ -695,11 +799,22 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
       }
       sx = P::add(sx, divd(0, m1, zc, q1, sm, sc, sp, dlo[0], dhi[0]));
     }
-    if (a.ndim >= 2) {
+    if (a.ndim >= 2 && ppm) {
+      V v[7];
+      v[H] = zc;
+#pragma unroll
+      for (int q = 0; q < X2N; ++q) {
+        const R *row = sr + (SX2 + q) * a.nap;
+        v[q < H ? q : q + 1] = (ANG && anypol && ypol[q]) ? P::mk(row[p0], row[p1]) : sv(row);
+      }
+      V loL, loR, hiL, hiR;
+      ppm_states<R>(v, loL, loR, hiL, hiR);
+      sx = P::add(sx, divs(1, loL, loR, hiL, hiR, dlo[1], dhi[1]));
+    } else if (a.ndim >= 2) {
       V yv[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const R *row = sr + (5 + q) * a.nap;
+        const R *row = sr + (SX2 + q) * a.nap;
         yv[q] = (ANG && anypol && ypol[q]) ? P::mk(row[p0], row[p1]) : sv(row);
       }
       V sm = zero, sc = zero, sp = zero;
@@ -712,8 +827,8 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
     }
     V divA = zero;
     if (ANG) {
-      // the own row of this cell is slot 2 of the staged x1 block
-      const R *row = sr + 2 * a.nap;
+      // the own row of this cell is slot h of the staged x1 block
+      const R *row = sr + H * a.nap;
       R da[2];
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
@@ -728,7 +843,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
     const V L = P::mk(-(sx.x + divA.x), -(sx.y + divA.y));
     V Us = P::fma(P::mk(dtR, dtR), L, P::mul(fconv, zc));
     if (ST2) {
-      const V U0 = P::mul(fconv, sv(sr + 10 * a.nap));
+      const V U0 = P::mul(fconv, sv(sr + SI0 * a.nap));
       Us = P::mul(P::mk(R(0.5), R(0.5)), P::add(U0, Us));
     }
     const V Is = P::mul(Us, inv_f);
@@ -812,7 +927,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
   }
 
   // ---- phase C: implicit update of every bin
-  bool bad = false;
+  V chk = zero;           // stays 0 unless a written value is not finite (0 * inf, 0 * nan = nan)
   const bool want_src = couple && a.src;
   for (int c = 0; c < (cons ? nc : 0); ++c) {
     const unsigned kOff = (unsigned)(k0 + c) * strideK;
@@ -834,12 +949,13 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 544 : kStageMaxThreads) k_sta
         if ((lane & 7) == 0) red[(c * nwarp + warp) * kNRedC + (lane >> 3)] = s;
       }
     }
-    out = P::mk((act0 && !g0) ? out.x : R(0), (act1 && !g1) ? out.y : R(0));
+    out = P::mul(out, keep);
     if (inpair) {
       *(V *)(Io + kOff + own) = out;
-      bad |= !isfinite(out.x) || !isfinite(out.y);
+      chk = P::fma(out, zero, chk);
     }
   }
+  const bool bad = !isfinite(chk.x) || !isfinite(chk.y);
   if (cons && __any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrNonFinite);
   if (want_src) {
     // ---- phase D: -dR^0_mu with dR^0_mu = n^0 M[mu][A] sum (I+ - I*) n^A dOmega

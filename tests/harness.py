@@ -99,7 +99,7 @@ def run_both(w, nsteps, precision="f64", recon="plm", coupling=None, dt=None, ta
     cmode = {"thermal": rad.RAD_COUPLE_THERMAL, "emissivity": rad.RAD_COUPLE_EMISSIVITY,
              "none": rad.RAD_COUPLE_NONE}[mode]
     o = rad.rad_opts_default(precision=rad.RAD_F64 if precision == "f64" else rad.RAD_F32,
-                             recon=rad.RAD_RECON_PLM if recon == "plm" else rad.RAD_RECON_DC,
+                             recon={"dc": rad.RAD_RECON_DC, "plm": rad.RAD_RECON_PLM, "ppm": rad.RAD_RECON_PPM}[recon],
                              coupling=cmode, tau_const=tau)
     for _ in range(nsteps):
         rad.rad_step(gc.ctx, Ig, gas_g, dt, o, src_g)

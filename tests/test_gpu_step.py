@@ -9,8 +9,9 @@ import numpy as np
 import pytest
 import torch
 
+import paper_2302_04283_gb300 as rad
 import workloads as W
-from tests.harness import rel_err, run_both
+from tests.harness import GpuCase, match_bins, rel_err, run_both
 
 pytestmark = pytest.mark.gpu
 
@@ -116,6 +117,86 @@ def test_optical_depth_weighted_flux_matches_oracle(name, n, level, prec, recon,
         v *= 0.3 / np.sqrt((v * v).sum(-1)).max()
         w["u"] = v / np.sqrt(1 - (v * v).sum(-1))[..., None]
     r = run_both(w, 1, prec, recon=recon, tau=C)
+    try:
+        tol = TOL64 if prec == "f64" else TOL32
+        assert rel_err(r["I_g"], r["I_o"]) < tol
+        assert rel_err(r["T_g"], r["T_o"]) < tol
+    finally:
+        r["gc"].close()
+
+
+def test_moving_equilibration_trajectory_f64():
+    """The moving equilibration of Sec. 3 (u^1 = 1 initially, gas advanced by
+    the returned source): 25 GPU steps follow the oracle's trajectory to
+    1e-11 (the oracle's agreement with the paper's ODE is pinned on CPU)."""
+    from tests.test_oracle_coupling import _gas_from_conserved, _golden
+    import oracle.step as OSS
+    g = _golden("static_equilibration.txt")
+    gam, rho0, aa, p0, E0 = g["gamma"][0], g["rho"][0], g["alpha_a"][0], g["p_gas0"][0], g["u_rad0"][0]
+    w = W.make("turb3d", n=(2, 2, 2), level=2)
+    w.update(rho=np.full(w["T"].shape, rho0), alpha_a=np.full(w["T"].shape, aa), alpha_s=np.zeros(w["T"].shape))
+    from tests.harness import oracle_setup
+    st = oracle_setup(w)
+    gc = GpuCase(w)
+    try:
+        gmap = match_bins(gc.dir, st.ang.dir.numpy())
+        sh = w["T"].shape
+        dO = st.ang.dOmega.numpy()
+        u00 = math.sqrt(2.0)
+        D = rho0 * u00
+        wgas = rho0 + gam / (gam - 1) * p0
+        state = {"o": [wgas * 2.0 - p0, wgas * u00, rho0, p0, 1.0], "g": [wgas * 2.0 - p0, wgas * u00, rho0, p0, 1.0]}
+        I_o = torch.full(sh + (len(dO),), E0 / (4 * math.pi), dtype=torch.float64)
+        I_g = gc.to_gpu_I(I_o.numpy(), gmap, torch.float64)
+        dt = 0.4
+        for s in range(25):
+            Eg, Sx, rho, p, u1 = state["o"]
+            gas = {"rho": torch.full(sh, rho, dtype=torch.float64), "alpha_a": torch.full(sh, aa, dtype=torch.float64),
+                   "alpha_s": torch.zeros(sh, dtype=torch.float64), "eta": None,
+                   "u": torch.tensor([u1, 0.0, 0.0], dtype=torch.float64).expand(sh + (3,)).clone()}
+            I_o, _, src_o, ok = OSS.rk2_step(I_o, torch.full(sh, p / rho, dtype=torch.float64), gas, dt, st,
+                                             OSS.Opts(recon="dc", gamma=gam))
+            Eg, Sx = Eg - float(src_o.flatten()[0]), Sx + float(src_o.flatten()[1])
+            state["o"] = [Eg, Sx, *_gas_from_conserved(D, Eg, Sx, gam)]
+            Eg, Sx, rho, p, u1 = state["g"]
+            gg = {"rho": torch.full(sh, rho, dtype=torch.float64, device="cuda"),
+                  "alpha_a": torch.full(sh, aa, dtype=torch.float64, device="cuda"),
+                  "alpha_s": torch.zeros(sh, dtype=torch.float64, device="cuda"), "eta": None,
+                  "u": torch.tensor([u1, 0.0, 0.0], dtype=torch.float64, device="cuda").expand(sh + (3,)).contiguous(),
+                  "T": torch.full(sh, p / rho, dtype=torch.float64, device="cuda")}
+            src_g = torch.zeros(sh + (4,), dtype=torch.float64, device="cuda")
+            rad.rad_step(gc.ctx, I_g, gg, dt, rad.rad_opts_default(precision=rad.RAD_F64, gamma=gam,
+                                                                   recon=rad.RAD_RECON_DC), src_g)
+            sg = src_g.cpu().numpy().reshape(-1, 4)[0]
+            Eg, Sx = Eg - float(sg[0]), Sx + float(sg[1])
+            state["g"] = [Eg, Sx, *_gas_from_conserved(D, Eg, Sx, gam)]
+        rad.rad_check(gc.ctx)
+        for a, b in zip(state["g"], state["o"]):
+            assert abs(a - b) <= 1e-11 * abs(b)
+        assert rel_err(gc.from_gpu_I(I_g, gmap), I_o.numpy()) < 1e-11
+    finally:
+        gc.close()
+
+
+
+PPM_CASES = [
+    # name, sizes, level, precision, steps, C (optical depth)
+    ("turb3d", (7, 5, 9), 2, "f64", 2, 0.0),            # flat 3D, periodic
+    ("turb3d", (7, 5, 9), 2, "f32", 2, 0.0),
+    ("turb3d", (4, 3, 37), 2, "f64", 1, 0.0),           # two x3 chunks
+    ("torus3d", (8, 6, 4), 2, "f64", 2, 0.0),           # Kerr-Schild: polar (3 ghosts), outflow, angular fluxes
+    ("torus3d_big", (6, 4, 4), 2, "f32", 1, 0.0),
+    ("adjoint2d", (10, 8, 1), 2, "f64", 1, 0.0),        # 2D
+    ("turb3d", (7, 5, 6), 2, "f64", 1, 3.0),            # with the optical-depth weighting
+]
+
+
+@pytest.mark.parametrize("name,n,level,prec,steps,C", PPM_CASES)
+def test_ppm_step_matches_oracle(name, n, level, prec, steps, C):
+    """PPM reconstruction (Colella & Woodward 1984; Sec. 2.3) against the
+    oracle: FP64 1e-12, FP32 2e-5."""
+    w = W.make(name, n=n, level=level)
+    r = run_both(w, steps, prec, recon="ppm", tau=C)
     try:
         tol = TOL64 if prec == "f64" else TOL32
         assert rel_err(r["I_g"], r["I_o"]) < tol

@@ -223,3 +223,76 @@ def test_static_equilibration_at_the_papers_time_resolutions():
         gaps.append(prev - Teq)
     assert gaps[0] < gaps[1] < gaps[2]
     assert gaps[2] < 0.1 * (T0 - Teq)                          # even one step per coupling time gets close
+
+
+def _gas_from_conserved(D, E, Sx, gam):
+    """(rho, p, u^1) of an ideal gas from rho u^0, w u^0 u^0 - p and w u^0 u^1."""
+    def resid(u1):
+        u0 = math.sqrt(1.0 + u1 * u1)
+        w = Sx / (u0 * u1)
+        rho = D / u0
+        p = (w - rho) * (gam - 1.0) / gam
+        return w * u0 * u0 - p - E
+    u1 = brentq(resid, 1e-12, 50.0, xtol=1e-15, rtol=1e-15)
+    u0 = math.sqrt(1.0 + u1 * u1)
+    w = Sx / (u0 * u1)
+    rho = D / u0
+    return rho, (w - rho) * (gam - 1.0) / gam, u1
+
+
+def test_moving_equilibration_follows_the_papers_ode():
+    """Sec. 3 "Equilibration", moving case (Eq. moving_equilibration): the
+    static set-up with initial u^1 = 1.  The coupled RK2 steps, with the gas
+    energy-momentum advanced by the returned source (-dR^0_mu) and the gas
+    state recovered from rho u^0, w u^0 u^0 - p, w u^0 u^1 after each step,
+    converge at first order in dt to the ODE system the paper prints for the
+    same angle bins; total energy and momentum are conserved."""
+    from scipy.integrate import solve_ivp
+    g = _golden("static_equilibration.txt")
+    gam, rho0, aa = g["gamma"][0], g["rho"][0], g["alpha_a"][0]
+    p0, E0, u10 = g["p_gas0"][0], g["u_rad0"][0], 1.0
+    st = box_setup(n=(1, 1, 1))
+    sh = st.grid.shape
+    dirs, dO = st.ang.dir.numpy(), st.ang.dOmega.numpy()
+    n1 = dirs[:, 0]
+    u00 = math.sqrt(1 + u10 ** 2)
+    D = rho0 * u00
+    w0 = rho0 + gam / (gam - 1) * p0
+    Eg0, S0 = w0 * u00 * u00 - p0, w0 * u00 * u10
+    I0 = np.full(len(dO), E0 / (4 * math.pi))
+
+    def rhs(t, y):
+        Eg, Sx, I = y[0], y[1], y[2:]
+        rho, p, u1 = _gas_from_conserved(D, Eg, Sx, gam)
+        u0 = math.sqrt(1 + u1 * u1)
+        T4 = (p / rho) ** 4
+        R00, R01, R11 = (I * dO).sum(), (I * n1 * dO).sum(), (I * n1 * n1 * dO).sum()
+        nb = u0 - u1 * n1
+        return np.concatenate([[aa * (u0 * R00 - u1 * R01 - T4 * u0), aa * (u0 * R01 - u1 * R11 - T4 * u1)],
+                               aa * (T4 / (4 * math.pi) * nb ** -3 - nb * I)])
+
+    t_end = 20.0
+    sol = solve_ivp(rhs, (0, t_end), np.concatenate([[Eg0, S0], I0]), rtol=1e-11, atol=1e-13, dense_output=True)
+    errs = []
+    for nsteps in (25, 50, 100):
+        dt = t_end / nsteps
+        I = torch.tensor(np.broadcast_to(I0, sh + (len(dO),)).copy())
+        Eg, Sx = Eg0, S0
+        rho, p, u1 = rho0, p0, u10
+        err = 0.0
+        for s in range(nsteps):
+            gas = gas_fields(sh, rho=rho, u=(u1, 0.0, 0.0), aa=aa)
+            T = torch.full(sh, p / rho, dtype=F64)
+            I, Tn, src, ok = S.rk2_step(I, T, gas, dt, st, S.Opts(recon="dc", gamma=gam))
+            assert ok.all()
+            Eg, Sx = Eg - float(src.flatten()[0]), Sx + float(src.flatten()[1])
+            rho, p, u1 = _gas_from_conserved(D, Eg, Sx, gam)
+            Ir = I.flatten(0, 2)[0].numpy()
+            # conservation of total energy and x-momentum
+            assert abs(Eg + (Ir * dO).sum() - (Eg0 + E0)) < 1e-11 * (Eg0 + E0)
+            assert abs(Sx + (Ir * n1 * dO).sum() - S0) < 1e-11 * S0
+            ref = sol.sol((s + 1) * dt)
+            err = max(err, abs(Eg - ref[0]) / ref[0], abs(Sx - ref[1]) / ref[1])
+        errs.append(err)
+    assert errs[2] < 1e-2
+    assert 1.6 < errs[0] / errs[1] < 2.6 and 1.6 < errs[1] / errs[2] < 2.6
