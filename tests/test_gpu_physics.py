@@ -1,0 +1,116 @@
+"""The CUDA path against closed-form solutions the paper prints for its
+tests (Sec. 3), run on the GPU at the paper's sizes:
+
+* static diffusion (Sec. 3, "Diffusion"): a Gaussian radiation pulse in a
+  purely scattering static medium, alpha_s = 1e4, sigma = 0.1, intensities
+  from the Minerbo closure (f <= 1/3 branch), t = 50, PLM: the L1 error of
+  E against Eq. diffusion falls at least at second order in the cell count;
+* plane-parallel hohlraum (Sec. 3, "Hohlraums"): radiation off a wall of
+  energy density 1 into vacuum, 128 cells, t = 3/4: the moment error of the
+  paper's norm decreases with the number of angles.  The wall is an
+  optically thick emitting slab (alpha = 1e4, source function 1/4 pi) ahead
+  of x = 0, which emits the isotropic wall intensity to within O(1/(alpha dx)).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2302_04283_gb300 as rad
+
+pytestmark = pytest.mark.gpu
+
+
+def _flat_1d(level, xf):
+    ctx = rad.rad_create(torch.cuda.current_stream())
+    na, nap = rad.rad_init_angles(ctx, level)
+    d, dO, _ = rad.rad_get_angles(ctx, na)
+    rad.rad_set_metric(ctx, "mink_cart", 0.0, 1, [xf, np.array([0.0, 1.0]), np.array([0.0, 1.0])],
+                       (("outflow", "outflow"), ("periodic",) * 2, ("periodic",) * 2))
+    return ctx, na, nap, d, dO
+
+
+def _gas(M, alpha_a, alpha_s, eta):
+    t = lambda a: torch.tensor(np.broadcast_to(a, (M,)).copy(), dtype=torch.float64, device="cuda").reshape(1, 1, M)
+    return {"rho": t(1.0), "u": torch.zeros(1, 1, M, 3, dtype=torch.float64, device="cuda"),
+            "alpha_a": t(alpha_a), "alpha_s": t(alpha_s), "eta": t(eta), "T": t(1.0)}
+
+
+def _diffusion_error(N, prec, level=1, sig=0.1, a_s=1e4, t_end=50.0):
+    xf = np.linspace(-1.0, 1.0, N + 1)
+    ctx, na, nap, d, dO = _flat_1d(level, xf)
+    try:
+        dt = rad.rad_cfl_dt(ctx, 0.3)
+        nsteps = int(math.ceil(t_end / dt))
+        dt = t_end / nsteps
+        xc = 0.5 * (xf[1:] + xf[:-1])
+        E = np.exp(-xc ** 2 / (2 * sig ** 2))
+        F = xc / (3.0 * a_s * sig ** 2) * E                 # -(dE/dx) / (3 alpha_s)
+        I = np.zeros((1, 1, N, nap))
+        I[0, 0, :, :na] = (E[:, None] + 3.0 * d[None, :, 0] * F[:, None]) / (4 * math.pi)   # Minerbo, f <= 1/3
+        tdt = torch.float64 if prec == "f64" else torch.float32
+        Ig = torch.tensor(I, dtype=tdt, device="cuda")
+        gas = _gas(N, 0.0, a_s, 0.0)
+        o = rad.rad_opts_default(precision=rad.RAD_F64 if prec == "f64" else rad.RAD_F32,
+                                 coupling=rad.RAD_COUPLE_EMISSIVITY)
+        for _ in range(nsteps):
+            rad.rad_step(ctx, Ig, gas, dt, o)
+        torch.cuda.synchronize()
+        rad.rad_check(ctx)
+        Ec = (Ig[0, 0, :, :na].double().cpu().numpy() * dO[None, :]).sum(-1)
+        A = (1 + 2 * t_end / (3 * a_s * sig ** 2)) ** -0.5
+        Ex = A * np.exp(-A * A * xc ** 2 / (2 * sig ** 2))
+        return float(np.abs(Ec - Ex).sum() * (2.0 / N))
+    finally:
+        rad.rad_destroy(ctx)
+
+
+def test_static_diffusion_converges_to_the_papers_solution():
+    errs = [_diffusion_error(N, "f64") for N in (128, 256, 512)]
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.5          # second order or better
+    assert errs[2] < 3e-3
+
+
+def test_static_diffusion_f32_matches_f64():
+    e64, e32 = _diffusion_error(256, "f64"), _diffusion_error(256, "f32")
+    assert abs(e32 - e64) < 0.1 * e64
+
+
+def _hohlraum_error(level, N=128, nslab=16, a_wall=1e4, t_end=0.75):
+    dx = 1.0 / N
+    xf = np.linspace(-nslab * dx, 1.0, N + nslab + 1)
+    ctx, na, nap, d, dO = _flat_1d(level, xf)
+    try:
+        dt = rad.rad_cfl_dt(ctx, 0.3)
+        nsteps = int(math.ceil(t_end / dt))
+        dt = t_end / nsteps
+        M = N + nslab
+        aa = np.zeros(M)
+        aa[:nslab] = a_wall
+        I = np.zeros((1, 1, M, nap))
+        I[0, 0, :nslab, :na] = 1.0 / (4 * math.pi)
+        Ig = torch.tensor(I, dtype=torch.float64, device="cuda")
+        gas = _gas(M, aa, 0.0, aa / (4 * math.pi))          # source function 1/4 pi in the wall
+        o = rad.rad_opts_default(precision=rad.RAD_F64, coupling=rad.RAD_COUPLE_EMISSIVITY)
+        for _ in range(nsteps):
+            rad.rad_step(ctx, Ig, gas, dt, o)
+        torch.cuda.synchronize()
+        rad.rad_check(ctx)
+        Iv = Ig[0, 0, nslab:, :na].cpu().numpy()
+        nx = d[:, 0]
+        R = [(Iv * dO).sum(-1), (Iv * nx * dO).sum(-1), (Iv * nx * nx * dO).sum(-1)]
+        s = np.clip((np.arange(N) + 0.5) * dx / t_end, 0.0, 1.0)
+        exact = [0.5 * (1 - s), 0.25 * (1 - s * s), (1 - s ** 3) / 6.0]
+        e = [np.abs(r - x).sum() * dx for r, x in zip(R, exact)]
+        return math.sqrt(sum(v * v for v in e) / 3.0)
+    finally:
+        rad.rad_destroy(ctx)
+
+
+def test_hohlraum_moments_converge_in_angle():
+    eps = {lev: _hohlraum_error(lev) for lev in (1, 2, 4, 8)}
+    assert eps[1] > eps[2] > eps[4] > eps[8]
+    # at least the half order the paper expects for this discontinuous field
+    assert eps[8] < eps[2] * math.sqrt(42.0 / 642.0)
+    assert eps[8] < 1e-3
