@@ -5,6 +5,9 @@ tests (Sec. 3), run on the GPU at the paper's sizes:
   purely scattering static medium, alpha_s = 1e4, sigma = 0.1, intensities
   from the Minerbo closure (f <= 1/3 branch), t = 50, PLM: the L1 error of
   E against Eq. diffusion falls at least at second order in the cell count;
+* advected diffusion: the same pulse in a medium moving at v = 0.02, started
+  on the surface tbar = -v xbar from the fluid-frame solution and judged in
+  the fluid frame at t = 50 on x in [-2, 1] (the pulse starts at x = -1);
 * plane-parallel hohlraum (Sec. 3, "Hohlraums"): radiation off a wall of
   energy density 1 into vacuum, 128 cells, t = 3/4: the moment error of the
   paper's norm decreases with the number of angles.  The wall is an
@@ -114,3 +117,50 @@ def test_hohlraum_moments_converge_in_angle():
     # at least the half order the paper expects for this discontinuous field
     assert eps[8] < eps[2] * math.sqrt(42.0 / 642.0)
     assert eps[8] < 1e-3
+
+
+def _diffusion_pulse(xb, tb, sig, a_s, x0):
+    A = (1 + 2 * tb / (3 * a_s * sig ** 2)) ** -0.5
+    return A * np.exp(-A * A * (xb - x0) ** 2 / (2 * sig ** 2)), A
+
+
+def _advected_diffusion_error(N, v=0.02, level=1, sig=0.1, a_s=1e4, t_end=50.0, x0=-1.0):
+    xf = np.linspace(-2.0, 1.0, 3 * N // 2 + 1)             # N cells per two units
+    ctx, na, nap, d, dO = _flat_1d(level, xf)
+    try:
+        dt = rad.rad_cfl_dt(ctx, 0.3)
+        nsteps = int(math.ceil(t_end / dt))
+        dt = t_end / nsteps
+        M = len(xf) - 1
+        xc = 0.5 * (xf[1:] + xf[:-1])
+        gam = 1.0 / math.sqrt(1.0 - v * v)
+        ux = gam * v
+        # fluid-frame state on the t = 0 surface: xbar = gam x, tbar = -gam v x
+        xb, tb = gam * xc, -gam * v * xc
+        Eb, A = _diffusion_pulse(xb, tb, sig, a_s, x0)
+        Fb = Eb * A * A * (xb - x0) / (3.0 * a_s * sig ** 2)  # -(dEbar/dxbar) / (3 alpha_s)
+        I = np.zeros((1, 1, M, nap))
+        for n in range(na):
+            nb0 = gam - ux * d[n, 0]                            # n^0bar = u^0 - u_x n^x
+            nbx = (gam * d[n, 0] - ux) / nb0                    # fluid-frame direction cosine
+            I[0, 0, :, n] = (Eb + 3.0 * nbx * Fb) / (4 * math.pi) / nb0 ** 4
+        Ig = torch.tensor(I, dtype=torch.float64, device="cuda")
+        gas = _gas(M, 0.0, a_s, 0.0)
+        gas["u"][..., 0] = ux
+        o = rad.rad_opts_default(precision=rad.RAD_F64, coupling=rad.RAD_COUPLE_EMISSIVITY)
+        for _ in range(nsteps):
+            rad.rad_step(ctx, Ig, gas, dt, o)
+        torch.cuda.synchronize()
+        rad.rad_check(ctx)
+        nb0 = gam - ux * d[:, 0]
+        Ebc = (Ig[0, 0, :, :na].cpu().numpy() * nb0[None, :] ** 2 * dO[None, :]).sum(-1)   # u_a u_b R^ab
+        Ebx, _ = _diffusion_pulse(gam * (xc - v * t_end), gam * (t_end - v * xc), sig, a_s, x0)
+        return float(np.abs(Ebc - Ebx).sum() * (xf[1] - xf[0]))
+    finally:
+        rad.rad_destroy(ctx)
+
+
+def test_advected_diffusion_converges_to_the_papers_solution():
+    errs = [_advected_diffusion_error(N) for N in (128, 256, 512)]
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.5
+    assert errs[2] < 3e-3
