@@ -95,6 +95,13 @@ template <typename R> __device__ __forceinline__ R fdiv(R a, R b) { return a / b
 __device__ __forceinline__ double rexpm1(double x) { return expm1(x); }
 __device__ __forceinline__ float rexpm1(float x) { return expm1f(x); }
 template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
+// hardware approximate reciprocal (one MUFU op, within an ulp or so); the FP32
+// path's stated tolerance covers it
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 
 // PLM half-slope q = dl dr / (dl + dr) if dl dr > 0 else 0 (van Leer 1974).
 template <typename R>
@@ -223,7 +230,7 @@ template <> struct P2<float> {
   static __device__ __forceinline__ V mul(V a, V b) { return __fmul2_rn(a, b); }
   static __device__ __forceinline__ V fma(V a, V b, V c) { return __ffma2_rn(a, b, c); }
   // approximate reciprocal (MUFU, ~1 ulp): the FP32 path's stated tolerance allows it
-  static __device__ __forceinline__ V rcp(V a) { return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y)); }
+  static __device__ __forceinline__ V rcp(V a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
 };
 template <> struct P2<double> {
   using V = double2;
@@ -244,8 +251,13 @@ __device__ __forceinline__ typename P2<R>::V vl2(typename P2<R>::V x, typename P
   auto s = P::add(dl, dr);
   // both quotients are formed unconditionally and the select discards the
   // ones of non-positive products (including 0/0), so no branch is taken
-  const R qx = fdiv(prod.x, s.x), qy = fdiv(prod.y, s.y);
-  return P::mk(prod.x > R(0) ? qx : R(0), prod.y > R(0) ? qy : R(0));
+  if constexpr (sizeof(R) == 4) {
+    const auto q = P::mul(prod, P::rcp(s));                    // one packed multiply
+    return P::mk(prod.x > R(0) ? q.x : R(0), prod.y > R(0) ? q.y : R(0));
+  } else {
+    const R qx = fdiv(prod.x, s.x), qy = fdiv(prod.y, s.y);
+    return P::mk(prod.x > R(0) ? qx : R(0), prod.y > R(0) ? qy : R(0));
+  }
 }
 
 template <typename R>
@@ -410,10 +422,11 @@ __host__ __device__ constexpr size_t stage_smem(int threads, int nap, int kc, in
 }
 
 template <typename R, bool ANG, int RC, bool ST2, bool TAU>
-// Register budget: the FP32 DC / PLM kernels are held to 96 registers (the
-// bound of a 544-thread block) so that five 128-thread CTAs fit an SM; FP64
-// and PPM ones get 128.
-__global__ void __launch_bounds__((sizeof(R) == 4 && RC != RAD_RECON_PPM) ? 544 : kStageMaxThreads) k_stage(StageArgs a) {
+// Register budget: the flat FP32 DC / PLM kernels are held to 96 registers
+// (the bound of a 544-thread block) so that five 128-thread CTAs fit an SM;
+// the others get 128 (the curved kernels' CTAs are limited by shared memory
+// first, and their angular-flux coefficients live in registers).
+__global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM) ? 544 : kStageMaxThreads) k_stage(StageArgs a) {
   using Col = typename GeoTypes<R>::Col;
   using Face = typename GeoTypes<R>::Face;
   using P = P2<R>;
@@ -589,6 +602,9 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && RC != RAD_RECON_PPM) ? 544 
   R a_self[2] = {R(0), R(0)}, a_nb[2][kMaxSlots];
   int nb_m[2][kMaxSlots];
   if (ANG) {
+    // unrolled in FP32 so that the coefficients stay in registers; the FP64
+    // kernels keep them in local memory (they are bound by the FP64 pipe)
+#pragma unroll(sizeof(R) == 4 ? 2 : 1)
     for (int e = 0; e < 2; ++e) {
       const int n = b0 + e;
       const bool ac = n < a.nang;
@@ -840,8 +856,8 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && RC != RAD_RECON_PPM) ? 544 
       divA = P::mk(da[0], da[1]);
     }
     // U* = U^{s-1} + dt L   (stage 1)   or   U^0/2 + (U^1 + dt L)/2   (stage 2), L = -(divS + divA)
-    const V L = P::mk(-(sx.x + divA.x), -(sx.y + divA.y));
-    V Us = P::fma(P::mk(dtR, dtR), L, P::mul(fconv, zc));
+    if (ANG) sx = P::add(sx, divA);
+    V Us = P::fma(P::mk(-dtR, -dtR), sx, P::mul(fconv, zc));   // L = -(divS + divA)
     if (ST2) {
       const V U0 = P::mul(fconv, sv(sr + SI0 * a.nap));
       Us = P::mul(P::mk(R(0.5), R(0.5)), P::add(U0, Us));
