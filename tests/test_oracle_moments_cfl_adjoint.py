@@ -116,3 +116,86 @@ def test_step_vjp_dot_product(adj_case):
     lhs = float((lam * jvp).sum())
     rhs = float((lam_n * dI).sum() + (g_aa * da).sum())
     assert abs(lhs - rhs) < 1e-12 * max(abs(lhs), 1.0)
+
+
+def _chain_vjp(I0, T0, gas, dt, st, opts, nsteps):
+    """dL/d(I0, T0, alpha_a, alpha_s) of the outgoing-flux loss after nsteps,
+    by chaining one-step vector-Jacobian products backwards (lamT carries
+    the gradient through the gas temperature)."""
+    Is, Ts = [I0], [T0]
+    for _ in range(nsteps):
+        I, T, _, ok = S.rk2_step(Is[-1], Ts[-1], gas, dt, st, opts)
+        assert ok.all()
+        Is.append(I)
+        Ts.append(T)
+    lam, lamT = A.loss_seed(Is[-1], st), torch.zeros_like(T0)
+    ga, gs = torch.zeros_like(T0), torch.zeros_like(T0)
+    for s in reversed(range(nsteps)):
+        lam, lamT, g1, g2, _ = A.step_vjp(Is[s], Ts[s], gas, dt, st, opts, lam, lamT)
+        ga, gs = ga + g1, gs + g2
+    return float(A.loss_outer(Is[-1], st)), lam, lamT, ga, gs
+
+
+def test_thermal_gradient_matches_central_differences(adj_case):
+    """Thermal coupling: the temperature evolves through the quartic of
+    Sec. 2.5, so the gradient runs through its root (implicit-function
+    theorem) and through T from step to step.  Chained one-step VJPs
+    against central differences of the forward oracle for alpha_a, alpha_s
+    and the initial T, and against reverse-mode AD through all steps."""
+    w, st, gas, dt = adj_case
+    opts = S.Opts(mode="thermal")
+    I0, T0 = torch.tensor(w["I0"]), torch.tensor(w["T"])
+    nsteps = 3
+    L, lam, lamT, ga, gs = _chain_vjp(I0, T0, gas, dt, st, opts, nsteps)
+    L2, grads2 = A.gradient(I0, T0, gas, dt, st, opts, nsteps)
+    ga2, gs2 = grads2[0], grads2[1]
+    assert abs(L - float(L2)) <= 1e-14 * abs(L)
+    assert float((ga - ga2).abs().max()) <= 1e-12 * float(ga2.abs().max())
+    assert float((gs - gs2).abs().max()) <= 1e-12 * float(gs2.abs().max())
+
+    def loss_with(field, cell, h):
+        g2 = {k: (v.clone() if v is not None else None) for k, v in gas.items()}
+        T = T0.clone()
+        if field == "T":
+            T[cell] += h
+        else:
+            g2[field][cell] += h
+        I = I0
+        for _ in range(nsteps):
+            I, T, _, _ = S.rk2_step(I, T, g2, dt, st, opts)
+        return float(A.loss_outer(I, st))
+
+    for field, grad, base in (("alpha_a", ga, gas["alpha_a"]), ("alpha_s", gs, gas["alpha_s"]), ("T", lamT, T0)):
+        assert float(grad.abs().max()) > 0.0
+        for cell in [(0, 1, 5), (0, 2, 4), (0, 0, 3), (0, 3, 0)]:
+            # relative step 1e-4: roundoff (eps |L| / h) would dominate the
+            # small entries at 1e-5, and at 1e-3 a perturbation of T can
+            # cross a kink of the PLM limiter
+            h = 1e-4 * float(base[cell])
+            fd = (loss_with(field, cell, h) - loss_with(field, cell, -h)) / (2 * h)
+            ad = float(grad[cell])
+            assert abs(fd - ad) <= 1e-6 * max(abs(ad), 2e-2 * float(grad.abs().max())), (field, cell, fd, ad)
+
+
+def test_thermal_step_vjp_dot_product(adj_case):
+    """<(lam, lamT), J (dI, dT, dalpha)> = <J^T (lam, lamT), (dI, dT, dalpha)>
+    for the thermal step, with J (.) by forward-mode AD."""
+    w, st, gas, dt = adj_case
+    opts = S.Opts(mode="thermal")
+    I0, T0 = torch.tensor(w["I0"]), torch.tensor(w["T"])
+    rng = np.random.default_rng(9)
+    lam, lamT = torch.tensor(rng.normal(size=I0.shape)), torch.tensor(rng.normal(size=T0.shape))
+    dI, dT = torch.tensor(rng.normal(size=I0.shape)), torch.tensor(rng.normal(size=T0.shape))
+    da, ds = torch.tensor(rng.normal(size=T0.shape)), torch.tensor(rng.normal(size=T0.shape))
+    lam_n, lamT_n, g_aa, g_as, _ = A.step_vjp(I0, T0, gas, dt, st, opts, lam, lamT)
+
+    def f(I, T, aa, a_s):
+        g2 = dict(gas)
+        g2["alpha_a"], g2["alpha_s"] = aa, a_s
+        I2, T2, _, _ = S.rk2_step(I, T, g2, dt, st, opts)
+        return I2, T2
+
+    _, (jI, jT) = torch.func.jvp(f, (I0, T0, gas["alpha_a"], gas["alpha_s"]), (dI, dT, da, ds))
+    lhs = float((lam * jI).sum() + (lamT * jT).sum())
+    rhs = float((lam_n * dI).sum() + (lamT_n * dT).sum() + (g_aa * da).sum() + (g_as * ds).sum())
+    assert abs(lhs - rhs) < 1e-12 * max(abs(lhs), 1.0)
