@@ -405,20 +405,32 @@ def run_extras(args, dev):
     ga, gs, ge = (torch.zeros(sha, dtype=torch.float64, device=dev) for _ in range(3))
     Iw = Ia.clone()
     fwd = _time_steps(lambda: rad.rad_step(ctx, Iw, gA, dta, oa), 8, 2)
-    adj = _time_steps(lambda: rad.rad_step_adjoint(ctx, Ia, gA, dta, oa, lam, lam_n, ga, gs, ge), 8, 2)
+    adj = _time_steps(lambda: rad.rad_step_adjoint(ctx, Ia, gA, dta, oa, lam, lam_n, None, None, ga, gs, ge), 8, 2)
     # the same in FP32
     o32 = rad.rad_opts_default(precision=rad.RAD_F32, coupling=rad.RAD_COUPLE_EMISSIVITY)
     Ia32, lam32 = Ia.float(), lam.float()
     lam_n32, Iw32 = torch.empty_like(Ia32), Ia32.clone()
     fwd32 = _time_steps(lambda: rad.rad_step(ctx, Iw32, gA, dta, o32), 8, 2)
-    adj32 = _time_steps(lambda: rad.rad_step_adjoint(ctx, Ia32, gA, dta, o32, lam32, lam_n32, ga, gs, ge), 8, 2)
+    adj32 = _time_steps(lambda: rad.rad_step_adjoint(ctx, Ia32, gA, dta, o32, lam32, lam_n32, None, None, ga, gs, ge), 8, 2)
+    # thermal coupling (gradient through the quartic and the temperature), FP64
+    oth = rad.rad_opts_default(precision=rad.RAD_F64, coupling=rad.RAD_COUPLE_THERMAL)
+    gT = dict(gA, eta=None)
+    Tw = gT["T"].clone()
+    gTw = dict(gT, T=Tw)
+    lamT, lamT_n = torch.ones_like(Tw), torch.empty_like(Tw)
+    fwdT = _time_steps(lambda: rad.rad_step(ctx, Iw, gTw, dta, oth), 8, 2)
+    adjT = _time_steps(lambda: rad.rad_step_adjoint(ctx, Ia, gT, dta, oth, lam, lam_n, lamT, lamT_n, ga, gs, None),
+                       8, 2)
     rad.rad_check(ctx)
     rad.rad_destroy(ctx)
     out["adjoint_over_forward"] = {"ratio": adj / fwd, "fwd_ms_per_step": fwd, "adj_ms_per_step": adj,
                                    "ratio_f32": adj32 / fwd32, "fwd_ms_per_step_f32": fwd32,
                                    "adj_ms_per_step_f32": adj32,
+                                   "ratio_thermal": adjT / fwdT, "fwd_ms_per_step_thermal": fwdT,
+                                   "adj_ms_per_step_thermal": adjT,
                                    "workload": "adjoint2d: Kerr-Schild a=0.5, 256x128, level 4 (162 bins), "
-                                               "fixed-emissivity coupling; adjoint includes the recomputation"}
+                                               "fixed-emissivity coupling (ratio, ratio_f32) and thermal coupling "
+                                               "(ratio_thermal, FP64); adjoint includes the recomputation"}
     return out
 
 

@@ -234,16 +234,23 @@ int rad_step_host(rad_ctx *ctx, int n_items, const rad_host_item *items, double 
                   const rad_opts *opts, int nsteps, int frame, int method);
 
 /*
- * Reverse-mode step: given the state I_n (checkpoint, not modified) and the
- * adjoint lam_np1 = dL/dI_{n+1}, write lam_n = dL/dI_n and ACCUMULATE
- * (+=) dL/dalpha_a, dL/dalpha_s, dL/deta (device FP64 [k][j][i]) through
- * the step rad_step would take from I_n.  opts->coupling must be
- * RAD_COUPLE_EMISSIVITY or RAD_COUPLE_NONE (T frozen), and opts->tau_const
- * must be 0 (RAD_EUNSUPPORTED otherwise).  lam arrays use the intensity
- * layout and precision.  g_eta may be NULL.
+ * Reverse-mode step: given the state I_n (checkpoint, not modified), the gas
+ * state gas->T = T_n, and the adjoints lam_np1 = dL/dI_{n+1} and
+ * lamT_np1 = dL/dT_{n+1}, write lam_n = dL/dI_n and lamT_n = dL/dT_n and
+ * ACCUMULATE (+=) dL/dalpha_a, dL/dalpha_s, dL/deta (device FP64 [k][j][i])
+ * through the step rad_step would take from (I_n, T_n).  With
+ * RAD_COUPLE_THERMAL the gradient runs through the root of the quartic of
+ * Sec. 2.5 (implicit-function theorem) and through the temperature between
+ * the stages; with RAD_COUPLE_EMISSIVITY or RAD_COUPLE_NONE the temperature
+ * is frozen and lamT_n = lamT_np1.  opts->tau_const must be 0 and opts->recon
+ * DC or PLM (RAD_EUNSUPPORTED otherwise).  lam arrays use the intensity
+ * layout and precision; lamT arrays are device FP64 [k][j][i].  lamT_np1 may
+ * be NULL (zero), lamT_n may be NULL (not written) and may equal lamT_np1;
+ * g_eta may be NULL.
  */
 int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
                      const rad_opts *opts, const void *lam_np1, void *lam_n,
+                     const double *lamT_np1, double *lamT_n,
                      double *g_alpha_a, double *g_alpha_s, double *g_eta);
 
 /*

@@ -89,8 +89,8 @@ def lib():
         "rad_step": ([_vp, _vp, P(rad_gas), ctypes.c_double, P(rad_opts), _vp], ctypes.c_int),
         "rad_step_noalloc": ([_vp, _vp, P(rad_gas), ctypes.c_double, P(rad_opts), _vp], ctypes.c_int),
         "rad_moments": ([_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(rad_gas), _vp], ctypes.c_int),
-        "rad_step_adjoint": ([_vp, _vp, P(rad_gas), ctypes.c_double, P(rad_opts), _vp, _vp, _vp, _vp, _vp],
-                             ctypes.c_int),
+        "rad_step_adjoint": ([_vp, _vp, P(rad_gas), ctypes.c_double, P(rad_opts), _vp, _vp, _vp, _vp, _vp, _vp,
+                              _vp], ctypes.c_int),
         "rad_loss_outer": ([_vp, _vp, ctypes.c_int, _vp, _vp], ctypes.c_int),
         "rad_step_host": ([_vp, ctypes.c_int, P(rad_host_item), ctypes.c_double, P(rad_opts), ctypes.c_int,
                            ctypes.c_int, ctypes.c_int], ctypes.c_int),
@@ -219,11 +219,14 @@ def rad_moments(ctx, I, precision, frame, method, gas, R):
     _check(ctx, lib().rad_moments(ctx, _ptr(I), precision, frame, method, ctypes.byref(g), _ptr(R)))
 
 
-def rad_step_adjoint(ctx, I_n, gas, dt, opts, lam_np1, lam_n, g_alpha_a, g_alpha_s, g_eta=None):
+def rad_step_adjoint(ctx, I_n, gas, dt, opts, lam_np1, lam_n, lamT_np1, lamT_n, g_alpha_a, g_alpha_s,
+                     g_eta=None):
+    """lamT_np1 / lamT_n: adjoint of the gas temperature after / before the
+    step (FP64 [k][j][i] device tensors, or None)."""
     g = _gas(gas)
     _check(ctx, lib().rad_step_adjoint(ctx, _ptr(I_n), ctypes.byref(g), float(dt), ctypes.byref(opts),
-                                       _ptr(lam_np1), _ptr(lam_n), _ptr(g_alpha_a), _ptr(g_alpha_s),
-                                       _ptr(g_eta)))
+                                       _ptr(lam_np1), _ptr(lam_n), _ptr(lamT_np1), _ptr(lamT_n),
+                                       _ptr(g_alpha_a), _ptr(g_alpha_s), _ptr(g_eta)))
 
 
 def rad_loss_outer(ctx, I, precision, L_dev, dL_dI=None):

@@ -5,6 +5,10 @@ I and, on the backward pass, rad_step_adjoint from the saved checkpoint I
 (per-step checkpointing with recomputation inside the library).  The
 gradient flows to I, alpha_a, alpha_s and eta.  Coupling must be the
 fixed-emissivity (or no) coupling, where the gas temperature is frozen.
+
+RadStepThermalFn.apply(I, T, alpha_a, alpha_s, step) is the same for the
+thermal coupling: it returns (I, T) after the step, and the gradient flows
+to I, T, alpha_a and alpha_s (through the quartic's root).
 """
 import torch
 
@@ -44,8 +48,37 @@ class RadStepFn(torch.autograd.Function):
         g_aa = torch.zeros_like(aa)
         g_as = torch.zeros_like(as_)
         g_eta = torch.zeros_like(eta) if fctx.has_eta else None
-        rad_step_adjoint(cfg.ctx, I_n, gas, cfg.dt, cfg.opts, lam.contiguous(), lam_n, g_aa, g_as, g_eta)
+        rad_step_adjoint(cfg.ctx, I_n, gas, cfg.dt, cfg.opts, lam.contiguous(), lam_n, None, None, g_aa, g_as,
+                         g_eta)
         return lam_n, g_aa, g_as, g_eta, None
+
+
+class RadStepThermalFn(torch.autograd.Function):
+    @staticmethod
+    def forward(fctx, I, T, alpha_a, alpha_s, cfg):
+        gas = dict(cfg.gas)
+        T_out = T.detach().clone()
+        gas.update(alpha_a=alpha_a.detach(), alpha_s=alpha_s.detach(), eta=None, T=T_out)
+        out = I.detach().clone()
+        rad_step(cfg.ctx, out, gas, cfg.dt, cfg.opts)
+        fctx.save_for_backward(I.detach(), T.detach(), alpha_a.detach(), alpha_s.detach())
+        fctx.cfg = cfg
+        return out, T_out
+
+    @staticmethod
+    def backward(fctx, lam, lamT):
+        I_n, T_n, aa, as_ = fctx.saved_tensors
+        cfg = fctx.cfg
+        gas = dict(cfg.gas)
+        gas.update(alpha_a=aa, alpha_s=as_, eta=None, T=T_n)
+        lam = torch.zeros_like(I_n) if lam is None else lam.contiguous()
+        lamT = None if lamT is None else lamT.contiguous()
+        lam_n = torch.empty_like(I_n)
+        lamT_n = torch.empty_like(T_n)
+        g_aa = torch.zeros_like(aa)
+        g_as = torch.zeros_like(as_)
+        rad_step_adjoint(cfg.ctx, I_n, gas, cfg.dt, cfg.opts, lam, lam_n, lamT, lamT_n, g_aa, g_as, None)
+        return lam_n, lamT_n, g_aa, g_as, None
 
 
 class OuterLossFn(torch.autograd.Function):

@@ -5,7 +5,10 @@
 // runs the stages backwards:
 //   coupling adjoint   lambda_I+  ->  mu = lambda_U* = lambda_I* / (n^0 n_0),
 //                      and dL/d(alpha_a, alpha_s, eta) of this coupling
-//                      (k_couple_adj: per-cell reductions, as in the forward)
+//                      (k_couple_adj: per-cell reductions, as in the forward);
+//                      with thermal coupling also lambda_T+ -> lambda_T-,
+//                      through the root of the quartic by the implicit-function
+//                      theorem (dT+ = -(T^4 dB4 + T dB1 + dB0) / f'(T+))
 //   transport adjoint  mu -> lambda_{I^{s-1}} += b f mu + b beta dt J_L^T mu,
 //                      lambda_{I^0} += a f mu
 //                      (k_transport_adj: gather form of the transposed
@@ -111,6 +114,14 @@ struct AdjArgs {
   void *outB;           // outB (+)= wBf f mu (nullable)
   double wBf;
   int accB;
+  // thermal coupling: adjoint of the stage's output temperature (nullable =
+  // 0) and the destinations of wTa lambda_T- ((+)= by accTa) and
+  // wTb lambda_T- (=), both nullable
+  const double *lamTp;
+  double *outTa, *outTb;
+  double wTa, wTb;
+  int accTa;
+  const ColGeo *cols64;  // FP64 column geometry (the thermal reverse sweep runs in FP64)
 };
 
 // Three-value CTA reduction used per cell: warp reduce-scatter, then every
@@ -129,12 +140,27 @@ __device__ __forceinline__ void cta_sum3(R v0, R v1, R v2, R *buf, int nwarp, in
   __syncthreads();
 }
 
-// Adjoint of the coupling of one stage (fixed emissivity or none).
+// The same for four values.
+template <typename R>
+__device__ __forceinline__ void cta_sum4(R v0, R v1, R v2, R v3, R *buf, int nwarp, int lane, int warp, R out[4]) {
+  R s = warp_reduce4(v0, v1, v2, v3, lane);
+  if ((lane & 7) == 0) buf[warp * 4 + (lane >> 3)] = s;
+  __syncthreads();
+  out[0] = out[1] = out[2] = out[3] = R(0);
+  for (int w = 0; w < nwarp; ++w) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) out[r] += buf[w * 4 + r];
+  }
+  __syncthreads();
+}
+
+// Adjoint of the coupling of one stage (thermal, fixed emissivity or none).
 template <typename R, int MAXT>
 __global__ void __launch_bounds__(MAXT) k_couple_adj(AdjArgs A) {
   using Col = typename GeoTypes<R>::Col;
   const StageArgs &a = A.s;
   __shared__ R buf[32 * 4];
+  __shared__ double dbuf[32 * 4], sc[8];
   const int n = threadIdx.x;
   const int nwarp = blockDim.x >> 5, lane = n & 31, warp = n >> 5;
   const bool act = n < a.nang;
@@ -170,7 +196,7 @@ __global__ void __launch_bounds__(MAXT) k_couple_adj(AdjArgs A) {
       continue;
     }
     const R ux = (R)a.u[3 * cell], uy = (R)a.u[3 * cell + 1], uz = (R)a.u[3 * cell + 2];
-    const R aE = (R)(a.aa[cell] + a.as[cell]), as = (R)a.as[cell], eta = (R)a.eta[cell];
+    const R aE = (R)(a.aa[cell] + a.as[cell]), as = (R)a.as[cell];
     const R u0 = sqrt(R(1) + ux * ux + uy * uy + uz * uz);
     const R Is = act ? Isv[e] : R(0);
     const R nb = u0 - (ux * nh0 + uy * nh1 + uz * nh2);
@@ -178,6 +204,94 @@ __global__ void __launch_bounds__(MAXT) k_couple_adj(AdjArgs A) {
     const R c1 = n0up * rden;
     const R c2n = c2pre * rden / (nb * nb * nb);
     const R wbar = nb * nb * dOm;
+    if (a.mode == RAD_COUPLE_THERMAL) {
+      // forward (Sec. 2.5): D = sum (c1 - 1) I* wbar, A2 = c2pre sum dOmega
+      // rden / n^0bar, Ebar- = sum I* wbar, the quartic B4 T^4 + B1 T + B0 = 0,
+      // Ebar+ = Ebar- - c_v (T+ - T-), S = alpha_a a T+^4 + alpha_s Ebar+,
+      // I+ = c1 I* + c2n S.  The reverse sweep runs in FP64 for both
+      // precisions (only I* and lambda_I+ are in the working precision): the
+      // terms of dL/dalpha_s cancel, and FP32 per-bin sums lose percents.
+      const ColGeo &cd = A.cols64[col];
+      double xh = 0.0, yh = 0.0, zh = 0.0, dOd = 0.0;
+      if (act) {
+        xh = a.dir[3 * n];
+        yh = a.dir[3 * n + 1];
+        zh = a.dir[3 * n + 2];
+        dOd = a.dOmega[n];
+      }
+      const double n0d = cd.n0up, dtsd = a.dts, c2pd = dtsd / kFourPi;
+      const double uxd = a.u[3 * cell], uyd = a.u[3 * cell + 1], uzd = a.u[3 * cell + 2];
+      const double aad = a.aa[cell], asd = a.as[cell], ar = a.a_rad;
+      const double nbd = sqrt(1.0 + uxd * uxd + uyd * uyd + uzd * uzd) - (uxd * xh + uyd * yh + uzd * zh);
+      const double nbaEd = nbd * (aad + asd) * dtsd;
+      const double rdend = 1.0 / (n0d + nbaEd);
+      const double c1d = n0d * rdend, cm1d = -nbaEd * rdend;          // c1 and c1 - 1
+      const double c2nd = c2pd * rdend / (nbd * nbd * nbd);
+      const double wbd = nbd * nbd * dOd;
+      const double Isd = act ? (double)Is : 0.0, lpd = (double)lamp;
+      double t4[4];
+      cta_sum4<double>(act ? cm1d * Isd * wbd : 0.0, act ? dOd * rdend / nbd : 0.0, act ? Isd * wbd : 0.0,
+                       act ? c2nd * lpd : 0.0, dbuf, nwarp, lane, warp, t4);
+      if (n == 0) {
+        const double D = t4[0], A2 = c2pd * t4[1], Em = t4[2], lS = t4[3];
+        const double Tm = a.stage2 ? 0.5 * (a.T0[cell] + a.T1[cell]) : a.T0[cell];
+        const double cv = a.rho[cell] * a.inv_gm1;
+        const double B4 = A2 * aad * ar, B1 = cv * (1.0 - A2 * asd), B0 = D + A2 * asd * Em - B1 * Tm;
+        bool ok = true;
+        const double Tp = quartic_root(B4, B1, B0, true, ok);
+        if (!ok || !isfinite(Tp)) atomicOr(a.err, kErrNoConv);
+        const double T3 = Tp * Tp * Tp, T4 = T3 * Tp;
+        const double Ep = Em - cv * (Tp - Tm);
+        // S = alpha_a a T+^4 + alpha_s Ebar+
+        double lT = (A.lamTp ? A.lamTp[cell] : 0.0) + 4.0 * aad * ar * T3 * lS;
+        const double lEp = asd * lS;
+        double laa = ar * T4 * lS, las = Ep * lS;
+        // Ebar+ = Ebar- - c_v T+ + c_v T-
+        double lEm = lEp, lTm = cv * lEp;
+        lT -= cv * lEp;
+        // T+ = root(B4, B1, B0): d/dB = -(T^4, T, 1) / f'(T+)
+        const double g = lT / (4.0 * B4 * T3 + B1);
+        const double lB4 = -g * T4, lB0 = -g;
+        double lB1 = -g * Tp;
+        // B0 = D + A2 alpha_s Ebar- - B1 T-
+        double lA2 = asd * Em * lB0;
+        las += A2 * Em * lB0;
+        lEm += A2 * asd * lB0;
+        lB1 -= Tm * lB0;
+        lTm -= B1 * lB0;
+        // B1 = c_v (1 - A2 alpha_s), B4 = A2 alpha_a a
+        lA2 += -cv * asd * lB1 + aad * ar * lB4;
+        las -= cv * A2 * lB1;
+        laa += A2 * ar * lB4;
+        sc[0] = aad * ar * T4 + asd * Ep;      // S
+        sc[1] = lB0;                           // lambda_D
+        sc[2] = lEm;
+        sc[3] = c2pd * lA2;                    // lambda of sum dOmega rden / n^0bar
+        sc[4] = laa;
+        sc[5] = las;
+        sc[6] = lTm;
+      }
+      __syncthreads();
+      const double S = sc[0], lD = sc[1], lEm = sc[2], lA2s = sc[3];
+      const double lc1 = Isd * lpd + Isd * wbd * lD;
+      const double lIs = c1d * lpd + cm1d * wbd * lD + wbd * lEm;
+      const double lrden = n0d * lc1 + c2pd / (nbd * nbd * nbd) * S * lpd + dOd / nbd * lA2s;
+      double t2[4];
+      cta_sum4<double>(act ? -nbd * dtsd * rdend * rdend * lrden : 0.0, 0.0, 0.0, 0.0, dbuf, nwarp, lane, warp, t2);
+      if (n == 0) {
+        const double laE = t2[0];
+        A.g_aa[cell] += sc[4] + laE;
+        A.g_as[cell] += sc[5] + laE;
+        if (A.outTa) A.outTa[cell] = (A.accTa ? A.outTa[cell] : 0.0) + A.wTa * sc[6];
+        if (A.outTb) A.outTb[cell] = A.wTb * sc[6];
+      }
+      if (act) {
+        const double fd = n0d * (cd.M[0][0] + cd.M[0][1] * xh + cd.M[0][2] * yh + cd.M[0][3] * zh);
+        mu[e] = guard ? R(0) : (R)(lIs / fd);
+      }
+      continue;
+    }
+    const R eta = (R)a.eta[cell];
     R t[3];
     cta_sum3<R>(act ? c1 * Is * wbar : R(0), act ? dOm * rden / nb : R(0), act ? c2n * lamp : R(0), buf, nwarp,
                 lane, warp, t);
@@ -484,7 +598,8 @@ cudaError_t launch_couple_adj(const AdjArgs &A, cudaStream_t st) {
 }  // namespace
 
 int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt, const rad_opts *o,
-                   const void *lam_np1, void *lam_n, double *g_aa, double *g_as, double *g_eta, std::string &err) {
+                   const void *lam_np1, void *lam_n, const double *lamT_np1, double *lamT_n, double *g_aa,
+                   double *g_as, double *g_eta, std::string &err) {
   const DevGeom &G = ctx->geom;
   const bool f32 = o->precision == RAD_F32;
   const bool ang = G.kind != RAD_MINK_CART;
@@ -492,7 +607,7 @@ int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
   const size_t esz = f32 ? 4 : 8;
   const size_t ib = (ncell * ctx->ang.n_ap * esz + 255) / 256 * 256;
   const size_t tb = (ncell * sizeof(double) + 255) / 256 * 256;
-  const size_t need = 5 * ib + 2 * tb;
+  const size_t need = 5 * ib + 3 * tb;
   if (ctx->adj_bytes < need) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->adj_buf);
@@ -507,6 +622,18 @@ int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
   unsigned char *p = (unsigned char *)ctx->adj_buf;
   void *I1 = p, *I1s = p + ib, *I2s = p + 2 * ib, *mu = p + 3 * ib, *lamI1 = p + 4 * ib;
   double *T1 = (double *)(p + 5 * ib), *T2 = (double *)(p + 5 * ib + tb);
+  double *lamT1 = (double *)(p + 5 * ib + 2 * tb);   // adjoint of the stage-1 temperature
+  const bool thermal = o->coupling == RAD_COUPLE_THERMAL;
+  if (!thermal && lamT_n && lamT_n != lamT_np1) {
+    // the temperature passes through an uncoupled or fixed-emissivity step
+    const cudaError_t te = lamT_np1 ? cudaMemcpyAsync(lamT_n, lamT_np1, ncell * sizeof(double),
+                                                      cudaMemcpyDeviceToDevice, ctx->stream)
+                                    : cudaMemsetAsync(lamT_n, 0, ncell * sizeof(double), ctx->stream);
+    if (te != cudaSuccess) {
+      err = std::string("adjoint temperature copy failed: ") + cudaGetErrorString(te);
+      return RAD_ECUDA;
+    }
+  }
   // ---- forward recompute with the pre-coupling primitives kept
   StageArgs s = make_stage_args(ctx, gas, dt, o, nullptr);
   {
@@ -542,8 +669,20 @@ int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
   A.g_aa = g_aa;
   A.g_as = g_as;
   A.g_eta = g_eta;
+  A.cols64 = G.cols;
+  // temperature adjoint (thermal coupling): stage 2 takes lambda_T of the
+  // step's output, T- = (T^0 + T^1) / 2 splits its lambda_T- in halves to
+  // T^0 (lamT_n) and T^1 (lamT1); stage 1 takes lamT1 and adds its
+  // lambda_T- (T- = T^0) to lamT_n
+  A.lamTp = lamT_np1;
+  A.outTa = lamT_n;
+  A.wTa = 0.5;
+  A.accTa = 0;
+  A.outTb = lamT1;
+  A.wTb = 0.5;
   if (ce == cudaSuccess) {
     A.s.dts = 0.5 * dt;
+    A.s.stage2 = 1;
     A.lam = lam_np1;
     A.Istar = I2s;
     A.mu = mu;
@@ -564,6 +703,12 @@ int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
   // ---- stage 1 backwards
   if (ce == cudaSuccess) {
     A.s.dts = dt;
+    A.s.stage2 = 0;
+    A.lamTp = lamT1;
+    A.outTa = lamT_n;
+    A.wTa = 1.0;
+    A.accTa = 1;
+    A.outTb = nullptr;
     A.lam = lamI1;
     A.Istar = I1s;
     A.mu = mu;

@@ -309,14 +309,13 @@ int rad_moments(rad_ctx *ctx, const void *I, int precision, int frame, int metho
 }
 
 int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt, const rad_opts *o,
-                     const void *lam_np1, void *lam_n, double *g_aa, double *g_as, double *g_eta) {
+                     const void *lam_np1, void *lam_n, const double *lamT_np1, double *lamT_n, double *g_aa,
+                     double *g_as, double *g_eta) {
   if (!ctx) return RAD_EINVAL;
   if (!ctx->have_metric) return fail(ctx, RAD_ESTATE, "rad_set_metric has not been called");
   int st = check_opts(ctx, o);
   if (st != RAD_OK) return st;
   if ((st = check_gas(ctx, gas, o, true)) != RAD_OK) return st;
-  if (o->coupling == RAD_COUPLE_THERMAL)
-    return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers fixed-emissivity and uncoupled steps");
   if (o->tau_const != 0.0)
     return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers the free-streaming flux (tau_const = 0)");
   if (o->recon == RAD_RECON_PPM)
@@ -326,7 +325,7 @@ int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double d
   if (ctx->ang.level > rad::kMaxLevelStep)
     return fail(ctx, RAD_EUNSUPPORTED, "rad_step_adjoint supports geodesic levels up to 9");
   std::string err;
-  st = rad::launch_adjoint(ctx, I_n, gas, dt, o, lam_np1, lam_n, g_aa, g_as, g_eta, err);
+  st = rad::launch_adjoint(ctx, I_n, gas, dt, o, lam_np1, lam_n, lamT_np1, lamT_n, g_aa, g_as, g_eta, err);
   return st == RAD_OK ? st : fail(ctx, st, err);
 }
 

@@ -143,8 +143,8 @@ int launch_moments(rad_ctx *ctx, const void *I, int precision, int frame, int me
 
 // adjoint.cu
 int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
-                   const rad_opts *opts, const void *lam_np1, void *lam_n, double *g_aa,
-                   double *g_as, double *g_eta, std::string &err);
+                   const rad_opts *opts, const void *lam_np1, void *lam_n, const double *lamT_np1,
+                   double *lamT_n, double *g_aa, double *g_as, double *g_eta, std::string &err);
 int launch_loss(rad_ctx *ctx, const void *I, int precision, double *L, void *dL, std::string &err);
 
 }  // namespace rad

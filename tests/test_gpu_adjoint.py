@@ -58,7 +58,7 @@ def test_step_vjp_matches_oracle(name, n, level, recon):
         ga = torch.zeros_like(gas["rho"])
         gs = torch.zeros_like(ga)
         ge = torch.zeros_like(ga)
-        rad.rad_step_adjoint(gc.ctx, Ig, gas, dt, o, lg, ln, ga, gs, ge)
+        rad.rad_step_adjoint(gc.ctx, Ig, gas, dt, o, lg, ln, None, None, ga, gs, ge)
         torch.cuda.synchronize()
         rad.rad_check(gc.ctx)
         assert rel_err(gc.from_gpu_I(ln, gmap), lam_o.numpy()) < 1e-11
@@ -168,12 +168,165 @@ def test_step_vjp_f32_matches_oracle(name, n, level):
         ga = torch.zeros_like(gas["rho"])
         gs = torch.zeros_like(ga)
         ge = torch.zeros_like(ga)
-        rad.rad_step_adjoint(gc.ctx, Ig, gas, dt, o, lg, ln, ga, gs, ge)
+        rad.rad_step_adjoint(gc.ctx, Ig, gas, dt, o, lg, ln, None, None, ga, gs, ge)
         torch.cuda.synchronize()
         rad.rad_check(gc.ctx)
         assert rel_err(gc.from_gpu_I(ln, gmap), lam_o.numpy()) < 2e-4
         assert rel_err(ga.cpu().numpy(), ga_o.numpy()) < 2e-4
         assert rel_err(gs.cpu().numpy(), gs_o.numpy()) < 2e-4
         assert rel_err(ge.cpu().numpy(), ge_o.numpy()) < 2e-4
+    finally:
+        gc.close()
+
+
+def _thermal_workload(name, n, level):
+    w = W.make(name, n=n, level=level)
+    w["mode"], w["eta"] = "thermal", None
+    return w
+
+
+@pytest.mark.parametrize("name,n,level,recon", [
+    ("adjoint2d", (10, 8, 1), 2, "plm"),
+    ("turb3d", (6, 5, 7), 2, "plm"),            # flat, periodic, moving gas
+    ("torus3d", (6, 6, 4), 2, "dc"),            # Kerr-Schild 3D, polar
+    ("torus3d_big", (5, 4, 4), 1, "plm"),       # moving gas and scattering in Kerr-Schild
+])
+def test_thermal_step_vjp_matches_oracle(name, n, level, recon):
+    """Thermal coupling: the adjoint through the quartic's root and the
+    temperature (lamT in and out) against the oracle's reverse mode, FP64:
+    1e-11 relative per output, and 2e-10 for dL/dalpha_s, whose terms
+    (through S, B0, B1 and alpha_E) cancel: on the torus case (alpha_s = 0)
+    the oracle's own dL/dalpha_s moves by 2.9e-11 relative when its inputs
+    are perturbed by 1e-15."""
+    w = _thermal_workload(name, n, level)
+    st = oracle_setup(w)
+    gc = GpuCase(w)
+    try:
+        gmap = match_bins(gc.dir, st.ang.dir.numpy())
+        dt = OCFL.cfl_dt(st, w["cfl"])
+        rng = np.random.default_rng(11)
+        lam, lamT = rng.normal(size=w["I0"].shape), rng.normal(size=w["T"].shape)
+        I0, T0 = torch.tensor(w["I0"]), torch.tensor(w["T"])
+        lam_o, lamT_o, ga_o, gs_o, _ = OA.step_vjp(I0, T0, oracle_gas(w), dt, st, OS.Opts(recon=recon),
+                                                   torch.tensor(lam), torch.tensor(lamT))
+        o = rad.rad_opts_default(precision=rad.RAD_F64, coupling=rad.RAD_COUPLE_THERMAL,
+                                 recon=rad.RAD_RECON_PLM if recon == "plm" else rad.RAD_RECON_DC)
+        Ig = gc.to_gpu_I(w["I0"], gmap, torch.float64)
+        lg = gc.to_gpu_I(lam, gmap, torch.float64)
+        ln = torch.zeros_like(Ig)
+        gas = gc.gas(w)
+        lTg = torch.tensor(lamT, device="cuda")
+        lTn = torch.zeros_like(lTg)
+        ga = torch.zeros_like(gas["rho"])
+        gs = torch.zeros_like(ga)
+        rad.rad_step_adjoint(gc.ctx, Ig, gas, dt, o, lg, ln, lTg, lTn, ga, gs, None)
+        torch.cuda.synchronize()
+        rad.rad_check(gc.ctx)
+        assert rel_err(gc.from_gpu_I(ln, gmap), lam_o.numpy()) < 1e-11
+        assert rel_err(lTn.cpu().numpy(), lamT_o.numpy()) < 1e-11
+        assert rel_err(ga.cpu().numpy(), ga_o.numpy()) < 1e-11
+        assert rel_err(gs.cpu().numpy(), gs_o.numpy()) < 2e-10
+        # lamT_n may alias lamT_np1 (in place)
+        ln2 = torch.zeros_like(Ig)
+        ga2, gs2 = torch.zeros_like(ga), torch.zeros_like(ga)
+        rad.rad_step_adjoint(gc.ctx, Ig, gas, dt, o, lg, ln2, lTg, lTg, ga2, gs2, None)
+        torch.cuda.synchronize()
+        assert torch.equal(lTg, lTn) and torch.equal(ln2, ln) and torch.equal(ga2, ga)
+    finally:
+        gc.close()
+
+
+@pytest.mark.parametrize("name,n,level", [("adjoint2d", (10, 8, 1), 2), ("torus3d", (6, 6, 4), 2)])
+def test_thermal_step_vjp_f32_matches_oracle(name, n, level):
+    """The FP32 thermal adjoint against the oracle's FP64 reverse mode;
+    tolerance 2e-4 relative per output, as for the fixed-emissivity FP32
+    adjoint (the per-cell chain through the quartic is FP64 on both sides)."""
+    w = _thermal_workload(name, n, level)
+    st = oracle_setup(w)
+    gc = GpuCase(w)
+    try:
+        gmap = match_bins(gc.dir, st.ang.dir.numpy())
+        dt = OCFL.cfl_dt(st, w["cfl"])
+        rng = np.random.default_rng(12)
+        lam, lamT = rng.normal(size=w["I0"].shape), rng.normal(size=w["T"].shape)
+        I0, T0 = torch.tensor(w["I0"]), torch.tensor(w["T"])
+        lam_o, lamT_o, ga_o, gs_o, _ = OA.step_vjp(I0, T0, oracle_gas(w), dt, st, OS.Opts(),
+                                                   torch.tensor(lam), torch.tensor(lamT))
+        o = rad.rad_opts_default(precision=rad.RAD_F32, coupling=rad.RAD_COUPLE_THERMAL)
+        Ig = gc.to_gpu_I(w["I0"], gmap, torch.float32)
+        lg = gc.to_gpu_I(lam, gmap, torch.float32)
+        ln = torch.zeros_like(Ig)
+        gas = gc.gas(w)
+        lTg = torch.tensor(lamT, device="cuda")
+        lTn = torch.zeros_like(lTg)
+        ga = torch.zeros_like(gas["rho"])
+        gs = torch.zeros_like(ga)
+        rad.rad_step_adjoint(gc.ctx, Ig, gas, dt, o, lg, ln, lTg, lTn, ga, gs, None)
+        torch.cuda.synchronize()
+        rad.rad_check(gc.ctx)
+        assert rel_err(gc.from_gpu_I(ln, gmap), lam_o.numpy()) < 2e-4
+        assert rel_err(lTn.cpu().numpy(), lamT_o.numpy()) < 2e-4
+        assert rel_err(ga.cpu().numpy(), ga_o.numpy()) < 2e-4
+        assert rel_err(gs.cpu().numpy(), gs_o.numpy()) < 2e-4
+    finally:
+        gc.close()
+
+
+def test_thermal_multistep_gradient_matches_oracle():
+    """dL/d(alpha_a, alpha_s, T^0) of the outgoing-flux loss after 4 thermal
+    steps, through torch.autograd (RadStepThermalFn) on the GPU, against the
+    oracle's chained reverse mode; 1e-10 relative."""
+    from paper_2302_04283_gb300.autograd import RadStepThermalFn
+    from tests.test_oracle_moments_cfl_adjoint import _chain_vjp
+    w = _thermal_workload("adjoint2d", (12, 8, 1), 2)
+    st = oracle_setup(w)
+    gc = GpuCase(w)
+    try:
+        gmap = match_bins(gc.dir, st.ang.dir.numpy())
+        dt = OCFL.cfl_dt(st, w["cfl"])
+        nsteps = 4
+        Lo, _, lamT_o, ga_o, gs_o = _chain_vjp(torch.tensor(w["I0"]), torch.tensor(w["T"]), oracle_gas(w), dt, st,
+                                               OS.Opts(), nsteps)
+        o = rad.rad_opts_default(precision=rad.RAD_F64, coupling=rad.RAD_COUPLE_THERMAL)
+        t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+        aa, as_, T = t(w["alpha_a"]).requires_grad_(True), t(w["alpha_s"]).requires_grad_(True), \
+            t(w["T"]).requires_grad_(True)
+        cfg = StepConfig(gc.ctx, gc.gas(w), dt, o)
+        I, Tc = gc.to_gpu_I(w["I0"], gmap, torch.float64), T
+        for _ in range(nsteps):
+            I, Tc = RadStepThermalFn.apply(I, Tc, aa, as_, cfg)
+        L = OuterLossFn.apply(I, gc.ctx, rad.RAD_F64)
+        L.backward()
+        rad.rad_check(gc.ctx)
+        assert abs(float(L) - Lo) < 1e-12 * abs(Lo)
+        assert rel_err(aa.grad.cpu().numpy(), ga_o.numpy()) < 1e-10
+        assert rel_err(as_.grad.cpu().numpy(), gs_o.numpy()) < 1e-10
+        assert rel_err(T.grad.cpu().numpy(), lamT_o.numpy()) < 1e-10
+    finally:
+        gc.close()
+
+
+def test_frozen_temperature_passes_its_adjoint_through():
+    """Fixed-emissivity coupling leaves T unchanged, so lamT_n = lamT_np1
+    (and a NULL lamT_np1 gives zero)."""
+    w = _emissivity_workload("adjoint2d", (7, 6, 1), 1)
+    gc = GpuCase(w)
+    try:
+        dt = rad.rad_cfl_dt(gc.ctx, w["cfl"])
+        o = rad.rad_opts_default(precision=rad.RAD_F64, coupling=rad.RAD_COUPLE_EMISSIVITY)
+        gmap = np.arange(gc.n_ang)
+        Ig = gc.to_gpu_I(w["I0"], gmap, torch.float64)
+        lg = torch.ones_like(Ig)
+        gas = gc.gas(w)
+        lTg = torch.tensor(np.random.default_rng(3).normal(size=w["T"].shape), device="cuda")
+        lTn = torch.full_like(lTg, 7.0)
+        z = torch.zeros_like(gas["rho"])
+        rad.rad_step_adjoint(gc.ctx, Ig, gas, dt, o, lg, torch.zeros_like(Ig), lTg, lTn, z, z.clone(), None)
+        torch.cuda.synchronize()
+        assert torch.equal(lTn, lTg)
+        rad.rad_step_adjoint(gc.ctx, Ig, gas, dt, o, lg, torch.zeros_like(Ig), None, lTn, z, z.clone(), None)
+        torch.cuda.synchronize()
+        rad.rad_check(gc.ctx)
+        assert float(lTn.abs().max()) == 0.0
     finally:
         gc.close()
