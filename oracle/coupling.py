@@ -21,6 +21,24 @@ renormalised; units k_B/(mu m_p) = 1.
 Mode 'emissivity' replaces the thermal emission alpha_P a T^4 / (4 pi) by a
 given fluid-frame emissivity eta and keeps T fixed (the c_v -> infinity
 limit); Eq. coupling_rad then gives Ebar+ = (A1 + 4 pi A2 eta)/(1 - A2 alpha_s).
+
+Radiation-dominated velocity substitution (end of Sec. 2.5, option rad_dom):
+where the fluid-frame radiation energy Ebar- exceeds the gas inertial
+density rho + u_gas, the coupling uses, before and after, the velocity
+  u^a = (1 - f^a) u_gas^a + f^a u_rad^a
+with the radiation velocity v_rad^a = R^{0a} / R^{00} (tetrad frame, from
+the intensities entering the coupling), its four-velocity u_rad, the
+momentum densities T_gas^{0a} = w u_gas^0 u_gas^a and T_rad^{0a} =
+w u_rad^0 u_rad^a (w = rho + u_gas + p), the coupling force
+  G^a = -(alpha_P a T^4 + alpha_s Ebar) u^a - alpha_E u_b R^{ab}
+at the gas velocity, and the fractions
+  f^a = G^a dt / (T_rad^{0a} - T_gas^{0a}), clamped to [0, 1].
+Readings: the printed fraction carries an extra factor u^a in its
+denominator; it is read as f^a above (the fraction of the momentum gap that
+the force closes in dt): with the factor, f^a would be singular for every
+gas at rest.  f^a = 0 where the gap T_rad^{0a} - T_gas^{0a} is 0, and no
+substitution where no subluminal radiation frame exists (R^{00} <= 0 or
+|v_rad| >= 1).  u_gas = c_v T-, p = rho T- (k_B / (mu m_p) = 1).
 """
 import math
 
@@ -64,17 +82,55 @@ def quartic_root(B4, B1, B0, iters=200):
     return torch.where(ok, T, torch.zeros_like(T)), ok
 
 
-def couple(I, T, gas, dt, setup, a_rad=1.0, gamma=5.0 / 3.0, mode="thermal"):
+def substituted_velocity(I, T, gas, dt, setup, a_rad=1.0, gamma=5.0 / 3.0):
+    """The coupling velocity of the radiation-dominated substitution (Sec. 2.5).
+
+    Returns (u_sub [.., 3], f [.., 3], active [..]): u_sub equals the gas
+    velocity wherever the substitution is inactive (active False)."""
+    dOmega = setup.ang.dOmega
+    nhat = setup.ang.dir
+    u = gas["u"]
+    u0 = torch.sqrt(1.0 + (u * u).sum(-1))
+    nbar0 = u0[..., None] - torch.einsum("...i,ni->...n", u, nhat)
+    Ebar = (I * nbar0 ** 2 * dOmega).sum(-1)            # sum Ibar dOmega_bar
+    rho = gas["rho"]
+    cv = rho / (gamma - 1.0)
+    ugas = cv * T
+    # tetrad-frame moments R^{AB} of the intensities entering the coupling
+    n4 = torch.cat([torch.ones(nhat.shape[0], 1, dtype=I.dtype), nhat], dim=1)
+    R = torch.einsum("...n,nA,nB,n->...AB", I, n4, n4, dOmega)
+    R00, R0a = R[..., 0, 0], R[..., 0, 1:]
+    v = R0a / torch.where(R00 > 0.0, R00, torch.ones_like(R00))[..., None]
+    v2 = (v * v).sum(-1)
+    active = (Ebar > rho + ugas) & (R00 > 0.0) & (v2 < 1.0)
+    gam = 1.0 / torch.sqrt(torch.where(active, 1.0 - v2, torch.ones_like(v2)))
+    urad = gam[..., None] * v
+    w = rho + ugas + (gamma - 1.0) * ugas                 # rho + u_gas + p
+    Tgas = (w * u0)[..., None] * u
+    Trad = (w * gam)[..., None] * urad
+    aa, a_s = gas["alpha_a"], gas["alpha_s"]
+    # u_b R^{ab} with u_0 = -u^0 (orthonormal tetrad)
+    uR = -u0[..., None] * R[..., 1:, 0] + torch.einsum("...b,...ab->...a", u, R[..., 1:, 1:])
+    G = -(aa * a_rad * T ** 4 + a_s * Ebar)[..., None] * u - (aa + a_s)[..., None] * uR
+    gap = Trad - Tgas
+    f = torch.where(gap != 0.0, G * dt / torch.where(gap != 0.0, gap, torch.ones_like(gap)), torch.zeros_like(gap))
+    f = torch.where(active[..., None], f.clamp(0.0, 1.0), torch.zeros_like(f))
+    u_sub = torch.where(active[..., None], (1.0 - f) * u + f * urad, u)
+    return u_sub, f, active
+
+
+def couple(I, T, gas, dt, setup, a_rad=1.0, gamma=5.0 / 3.0, mode="thermal", rad_dom=False):
     """One implicit coupling of every cell over time dt (Sec. 2.5).
 
     I     [k, j, i, n] tetrad-frame primitive intensities after transport
     T     [k, j, i]    gas temperature before coupling
     gas   dict with rho, u [k, j, i, 3] (u^ihat), alpha_a, alpha_s, eta
+    rad_dom: apply the radiation-dominated velocity substitution.
     Returns (I+, T+, dR [k, j, i, 4] = change of R^0_mu, ok).
     """
     dOmega = setup.ang.dOmega
     nhat = setup.ang.dir
-    u = gas["u"]
+    u = substituted_velocity(I, T, gas, dt, setup, a_rad, gamma)[0] if rad_dom else gas["u"]
     u0 = torch.sqrt(1.0 + (u * u).sum(-1))
     nbar0 = u0[..., None] - torch.einsum("...i,ni->...n", u, nhat)
     n0 = setup.nup[..., 0]

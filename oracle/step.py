@@ -34,6 +34,7 @@ class Opts:
     gamma: float = 5.0 / 3.0
     couple: bool = True
     tau_const: float = 0.0      # C of the optical-depth flux weighting (0: free streaming)
+    rad_dom: bool = False       # radiation-dominated velocity substitution (Sec. 2.5)
 
 
 def operator_L(I, setup, opts, tau=None):
@@ -66,7 +67,7 @@ def rk2_step(I0, T0, gas, dt, setup, opts):
     U1s = U0 + dt * operator_L(I0, setup, opts, tau)
     I1s = to_primitive(U1s, setup, mask)
     if opts.couple:
-        I1, T1, dR1, ok1 = C.couple(I1s, T0, gas, dt, setup, opts.a_rad, opts.gamma, opts.mode)
+        I1, T1, dR1, ok1 = C.couple(I1s, T0, gas, dt, setup, opts.a_rad, opts.gamma, opts.mode, opts.rad_dom)
     else:
         I1, T1, dR1, ok1 = I1s, T0, torch.zeros(T0.shape + (4,), dtype=I0.dtype), torch.ones_like(T0, dtype=torch.bool)
     I1 = torch.where(mask, torch.zeros_like(I1), I1)
@@ -75,7 +76,8 @@ def rk2_step(I0, T0, gas, dt, setup, opts):
     I2s = to_primitive(U2s, setup, mask)
     Tm = 0.5 * (T0 + T1)
     if opts.couple:
-        I2, T2, dR2, ok2 = C.couple(I2s, Tm, gas, 0.5 * dt, setup, opts.a_rad, opts.gamma, opts.mode)
+        I2, T2, dR2, ok2 = C.couple(I2s, Tm, gas, 0.5 * dt, setup, opts.a_rad, opts.gamma, opts.mode,
+                                     opts.rad_dom)
     else:
         I2, T2, dR2, ok2 = I2s, Tm, torch.zeros_like(dR1), ok1
     I2 = torch.where(mask, torch.zeros_like(I2), I2)
