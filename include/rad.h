@@ -146,6 +146,16 @@ typedef struct {
                         averages of the two cells.  0 (default) is the
                         free-streaming flux.  > 0 needs gas u, alpha_a and
                         alpha_s; rad_step_adjoint requires 0. */
+  int rad_dom;       /* 1: radiation-dominated velocity substitution (end of
+                        Sec. 2.5) in every coupling: where the fluid-frame
+                        radiation energy exceeds rho + u_gas the coupling
+                        runs at u^a = (1 - f^a) u_gas^a + f^a u_rad^a, with
+                        u_rad from v_rad^a = R^{0a}/R^{00} and
+                        f^a = G^a dt / (T_rad^{0a} - T_gas^{0a}) clamped to
+                        [0, 1] (read without the printed extra factor u^a).
+                        Needs RAD_COUPLE_THERMAL; each stage then runs the
+                        transport and the coupling as two kernels.  Default 0;
+                        rad_step_adjoint requires 0. */
 } rad_opts;
 
 /* Fill *opts with the defaults above (FP64, PLM, thermal coupling). */

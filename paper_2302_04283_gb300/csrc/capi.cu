@@ -92,6 +92,7 @@ void rad_opts_default(rad_opts *o) {
   o->a_rad = 1.0;
   o->gamma = 5.0 / 3.0;
   o->tau_const = 0.0;
+  o->rad_dom = 0;
 }
 
 int rad_init_angles(rad_ctx *ctx, int level, int *n_ang_out, int *n_ang_padded_out) {
@@ -251,6 +252,9 @@ static int check_opts(rad_ctx *ctx, const rad_opts *o) {
   if (!(o->n0crit >= 0.0)) return fail(ctx, RAD_EINVAL, "n0crit must be >= 0");
   if (!(o->tau_const >= 0.0) || !std::isfinite(o->tau_const))
     return fail(ctx, RAD_EINVAL, "tau_const must be finite and >= 0");
+  if (o->rad_dom != 0 && o->rad_dom != 1) return fail(ctx, RAD_EINVAL, "rad_dom must be 0 or 1");
+  if (o->rad_dom && o->coupling != RAD_COUPLE_THERMAL)
+    return fail(ctx, RAD_EINVAL, "rad_dom applies to the thermal coupling");
   return RAD_OK;
 }
 
@@ -320,6 +324,8 @@ int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double d
     return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers the free-streaming flux (tau_const = 0)");
   if (o->recon == RAD_RECON_PPM)
     return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers DC and PLM reconstruction");
+  if (o->rad_dom)
+    return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers the coupling at the gas velocity (rad_dom = 0)");
   if (!I_n || !lam_np1 || !lam_n || !g_aa || !g_as) return fail(ctx, RAD_EINVAL, "null argument");
   if (!(dt > 0.0)) return fail(ctx, RAD_EINVAL, "dt must be > 0");
   if (ctx->ang.level > rad::kMaxLevelStep)

@@ -1,0 +1,230 @@
+// Coupling with the radiation-dominated velocity substitution (end of
+// Sec. 2.5), one stage at a time, after a transport-only k_stage launch.
+//
+// Per cell, with the intensities I* that enter the coupling (tetrad frame,
+// already zero in guarded bins):
+//   1. Ebar- at the gas velocity and the tetrad moments R^{AB} of I*; where
+//      Ebar- > rho + u_gas (u_gas = c_v T-), the radiation velocity
+//      v^a = R^{0a} / R^{00} (if |v| < 1), the momentum densities
+//      T_gas^{0a} = w u^0 u^a and T_rad^{0a} = w u_rad^0 u_rad^a
+//      (w = rho + u_gas + p), the force G^a = -(alpha_a a T-^4 +
+//      alpha_s Ebar-) u^a - alpha_E u_b R^{ab} and the fractions
+//      f^a = G^a dt_s / (T_rad^{0a} - T_gas^{0a}) clamped to [0, 1] give the
+//      coupling velocity u^a = (1 - f^a) u_gas^a + f^a u_rad^a;
+//   2. the coupling of Sec. 2.5 at that velocity (the sums D, A2, Ebar-, the
+//      quartic for T+, Ebar+, S, Eq. implicit_ii);
+//   3. I+ (zero in guarded bins) over I*, T+, and the gas source
+//      -(1/2 dR^1) in stage 1, -dR^2 added in stage 2.
+// One CTA per column and chunk of cells, one thread per bin; the per-bin
+// arithmetic and the reductions are FP64 in both precisions (the option is
+// a slow path next to the fused stage kernel).  The printed fraction has an
+// extra factor u^a in its denominator; it is read without it (with it, f^a
+// would be singular for any gas at rest).
+#include "step_kernel.cuh"
+
+namespace rad {
+
+namespace {
+
+struct RdArgs {
+  void *I;                      // I* in, I+ out (in place)
+  const double *Tm;             // T- of the stage
+  double *Tout;                 // T+ (may equal Tm)
+  const double *rho, *u, *aa, *as;
+  double *src;                  // nullable
+  int stage2;
+  double dts;
+  int n1, n2, n3, nap, nang, kc;
+  const ColGeo *cols64;
+  const void *colsR;            // ColGeo or ColGeoF (the guard's precision)
+  const double *dir, *dOmega;
+  int zero_guard;
+  double n0crit, a_rad, gamma, inv_gm1;
+  int *err;
+};
+
+// Block sum of K doubles: the totals land in thread 0's v.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double *buf, int nwarp, int lane, int warp) {
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  if (lane == 0)
+    for (int k = 0; k < K; ++k) buf[warp * K + k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < nwarp; ++w) s += buf[w * K + k];
+      v[k] = s;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(1024) k_couple_rd(RdArgs a) {
+  using Col = typename GeoTypes<R>::Col;
+  __shared__ double buf[32 * 11];
+  __shared__ double sc[8];
+  const int n = threadIdx.x;
+  const int nwarp = blockDim.x >> 5, lane = n & 31, warp = n >> 5;
+  const bool act = n < a.nang;
+  const int nchunk = (a.n3 + a.kc - 1) / a.kc;
+  const int col = blockIdx.x / nchunk, chunk = blockIdx.x % nchunk;
+  const int k0 = chunk * a.kc, nc = min(a.kc, a.n3 - k0);
+  const unsigned ncol = (unsigned)a.n1 * a.n2;
+  const ColGeo &cd = a.cols64[col];
+  const Col &cr = ((const Col *)a.colsR)[col];
+  double xh = 0.0, yh = 0.0, zh = 0.0, dO = 0.0;
+  bool keep = false;
+  if (act) {
+    xh = a.dir[3 * n];
+    yh = a.dir[3 * n + 1];
+    zh = a.dir[3 * n + 2];
+    dO = a.dOmega[n];
+    // the guard decision exactly as the stage kernel takes it
+    const R nl = fma((R)zh, cr.M[0][3], fma((R)yh, cr.M[0][2], fma((R)xh, cr.M[0][1], cr.M[0][0])));
+    keep = !(a.zero_guard && fabs((double)nl) < a.n0crit);
+  }
+  const double n0 = cd.n0up, c2p = a.dts / kFourPi;
+  R *Ip = (R *)a.I;
+  for (int c = 0; c < nc; ++c) {
+    const unsigned cell = (unsigned)(k0 + c) * ncol + col;
+    const size_t e = (size_t)cell * a.nap + (act ? n : 0);
+    const double Is = act ? (double)Ip[e] : 0.0;
+    const double ux = a.u[3 * cell], uy = a.u[3 * cell + 1], uz = a.u[3 * cell + 2];
+    // 1. E_bar- at the gas velocity and the tetrad moments of I*
+    {
+      const double nb = sqrt(1.0 + ux * ux + uy * uy + uz * uz) - (ux * xh + uy * yh + uz * zh);
+      const double w = Is * dO;
+      double v[11] = {w * nb * nb, w, w * xh, w * yh, w * zh, w * xh * xh, w * xh * yh, w * xh * zh,
+                      w * yh * yh, w * yh * zh, w * zh * zh};
+      block_sum<11>(v, buf, nwarp, lane, warp);
+      if (n == 0) {
+        const double Em = v[0], R00 = v[1];
+        const double R0[3] = {v[2], v[3], v[4]};
+        const double Rab[3][3] = {{v[5], v[6], v[7]}, {v[6], v[8], v[9]}, {v[7], v[9], v[10]}};
+        const double rho = a.rho[cell], Tm = a.Tm[cell];
+        const double ugas = rho * a.inv_gm1 * Tm;
+        double us[3] = {ux, uy, uz};
+        bool active = Em > rho + ugas && R00 > 0.0;
+        double vr[3] = {0.0, 0.0, 0.0}, v2 = 0.0;
+        if (active) {
+          for (int i = 0; i < 3; ++i) {
+            vr[i] = R0[i] / R00;
+            v2 += vr[i] * vr[i];
+          }
+          active = v2 < 1.0;
+        }
+        if (active) {
+          const double ug[3] = {ux, uy, uz};
+          const double u0 = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+          const double gr = 1.0 / sqrt(1.0 - v2);
+          const double w = rho + ugas + (a.gamma - 1.0) * ugas;
+          const double aa = a.aa[cell], as = a.as[cell];
+          const double T2 = Tm * Tm;
+          const double emit = aa * a.a_rad * T2 * T2 + as * Em;
+          for (int i = 0; i < 3; ++i) {
+            const double urad = gr * vr[i];
+            // u_b R^{ib} with u_0 = -u^0
+            const double uR = -u0 * R0[i] + ug[0] * Rab[i][0] + ug[1] * Rab[i][1] + ug[2] * Rab[i][2];
+            const double G = -emit * ug[i] - (aa + as) * uR;
+            const double gap = w * gr * urad - w * u0 * ug[i];
+            double f = gap != 0.0 ? G * a.dts / gap : 0.0;
+            f = fmin(fmax(f, 0.0), 1.0);
+            us[i] = (1.0 - f) * ug[i] + f * urad;
+          }
+        }
+        sc[0] = us[0];
+        sc[1] = us[1];
+        sc[2] = us[2];
+      }
+      __syncthreads();
+    }
+    // 2. the coupling at the chosen velocity
+    const double vx = sc[0], vy = sc[1], vz = sc[2];
+    const double nb = sqrt(1.0 + vx * vx + vy * vy + vz * vz) - (vx * xh + vy * yh + vz * zh);
+    const double aE = a.aa[cell] + a.as[cell];
+    const double nbaE = nb * aE * a.dts;
+    const double rden = 1.0 / (n0 + nbaE);
+    const double wbar = Is * nb * nb * dO;                  // Ibar dOmega_bar
+    {
+      double v[3] = {act ? -nbaE * rden * wbar : 0.0, act ? dO * rden / nb : 0.0, act ? wbar : 0.0};
+      block_sum<3>(v, buf, nwarp, lane, warp);
+      if (n == 0) {
+        const double D = v[0], A2 = c2p * v[1], Em = v[2];
+        const double Tm = a.Tm[cell];
+        const double aa = a.aa[cell], as = a.as[cell];
+        const double cv = a.rho[cell] * a.inv_gm1;
+        const double B4 = A2 * aa * a.a_rad, B1 = cv * (1.0 - A2 * as), B0 = D + A2 * as * Em - B1 * Tm;
+        bool ok = true;
+        const double Tp = quartic_root(B4, B1, B0, true, ok);
+        const double Ep = Em - cv * (Tp - Tm);
+        const double T2 = Tp * Tp;
+        const double S = aa * a.a_rad * T2 * T2 + as * Ep;
+        if (!ok || !isfinite(Tp) || !isfinite(S)) atomicOr(a.err, kErrNoConv);
+        sc[3] = S;
+        a.Tout[cell] = Tp;
+      }
+      __syncthreads();
+    }
+    // 3. Eq. implicit_ii, the guard, and the change of R^0_mu
+    const double Iplus = n0 * rden * Is + c2p * rden / (nb * nb * nb) * sc[3];
+    const double out = keep ? Iplus : 0.0;
+    if (act) {
+      Ip[e] = (R)out;
+      if (!isfinite(out)) atomicOr(a.err, kErrNonFinite);
+    }
+    if (a.src) {
+      const double d = act ? (Iplus - Is) * dO : 0.0;
+      double v[4] = {d, d * xh, d * yh, d * zh};
+      block_sum<4>(v, buf, nwarp, lane, warp);
+      if (n == 0) {
+        double *sp = a.src + 4 * cell;
+        for (int m = 0; m < 4; ++m) {
+          const double dR = n0 * (cd.M[m][0] * v[0] + cd.M[m][1] * v[1] + cd.M[m][2] * v[2] + cd.M[m][3] * v[3]);
+          sp[m] = a.stage2 ? sp[m] - dR : -0.5 * dR;
+        }
+      }
+    }
+    __syncthreads();                // sc and buf are reused by the next cell
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_couple_rd(const StageArgs &s, bool f32, const double *Tm, double *Tout, cudaStream_t st) {
+  RdArgs a;
+  a.I = s.Iout;
+  a.Tm = Tm;
+  a.Tout = Tout;
+  a.rho = s.rho;
+  a.u = s.u;
+  a.aa = s.aa;
+  a.as = s.as;
+  a.src = s.src;
+  a.stage2 = s.stage2;
+  a.dts = s.dts;
+  a.n1 = s.n1;
+  a.n2 = s.n2;
+  a.n3 = s.n3;
+  a.nap = s.nap;
+  a.nang = s.nang;
+  a.kc = 4;
+  a.cols64 = s.cols64;
+  a.colsR = s.cols;
+  a.dir = s.dir;
+  a.dOmega = s.dOmega;
+  a.zero_guard = s.zero_guard;
+  a.n0crit = s.n0crit;
+  a.a_rad = s.a_rad;
+  a.gamma = s.gamma;
+  a.inv_gm1 = s.inv_gm1;
+  a.err = s.err;
+  const int threads = (s.nang + 31) / 32 * 32;
+  const unsigned grid = (unsigned)((size_t)s.n1 * s.n2 * ((s.n3 + a.kc - 1) / a.kc));
+  if (f32) k_couple_rd<float><<<grid, threads, 0, st>>>(a);
+  else k_couple_rd<double><<<grid, threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace rad

@@ -102,6 +102,7 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
   }
   const bool f32 = o->precision == RAD_F32;
   a.cols = f32 ? (const void *)G.colsF : (const void *)G.cols;
+  a.cols64 = G.cols;
   a.f1 = f32 ? (const void *)G.f1F : (const void *)G.f1;
   a.f2 = f32 ? (const void *)G.f2F : (const void *)G.f2;
   a.f3 = f32 ? (const void *)G.f3F : (const void *)G.f3;
@@ -155,6 +156,11 @@ int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_
     const int rc = check_stage(a, f32, err);
     if (rc != RAD_OK) return rc;
   }
+  // rad_dom: each stage is the transport-only stage kernel (I* with the
+  // guard applied, T- in Tout) followed by the coupling kernel with the
+  // radiation-dominated velocity substitution, in place
+  const bool rd = o->rad_dom != 0;
+  if (rd) a.mode = RAD_COUPLE_NONE;
   // stage 1: I^0 -> I^1 (scratch), T^0 -> T^1 (scratch)
   a.Iprev = I;
   a.I0 = I;
@@ -165,6 +171,7 @@ int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_
   a.stage2 = 0;
   a.dts = dt;
   cudaError_t ce = launch_stage(a, f32, ang, ctx->stream);
+  if (ce == cudaSuccess && rd) ce = launch_couple_rd(a, f32, scratch_T, scratch_T, ctx->stream);
   if (ce != cudaSuccess) {
     err = std::string("stage 1 launch failed: ") + cudaGetErrorString(ce);
     return RAD_ECUDA;
@@ -179,6 +186,7 @@ int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_
   a.stage2 = 1;
   a.dts = 0.5 * dt;
   ce = launch_stage(a, f32, ang, ctx->stream);
+  if (ce == cudaSuccess && rd) ce = launch_couple_rd(a, f32, gas->T, gas->T, ctx->stream);
   if (ce != cudaSuccess) {
     err = std::string("stage 2 launch failed: ") + cudaGetErrorString(ce);
     return RAD_ECUDA;

@@ -67,6 +67,7 @@ struct StageArgs {
   int depth;                       // stages of the shared-memory ring (2..kMaxStages)
   int bc_lo[3], bc_hi[3];
   const void *cols;       // ColGeo or ColGeoF
+  const ColGeo *cols64;   // the FP64 columns (the separate coupling kernel of the rad_dom option)
   const void *f1, *f2, *f3;
   const double *dir, *dOmega, *edge_geo;
   const int *perm, *slot_nbr, *slot_edge, *edge_pq;
@@ -86,6 +87,9 @@ cudaError_t launch_stage_rp(const StageArgs &a, cudaStream_t st);
 // RAD_OK, or RAD_EUNSUPPORTED with a message when a stage launch of this
 // grid / bin count cannot be formed (element count, shared memory, threads).
 int check_stage(const StageArgs &a, bool f32, std::string &err);
+// Coupling with the radiation-dominated velocity substitution (raddom.cu):
+// I* in s.Iout -> I+, T- (Tm) -> T+ (Tout), the gas source of stage s.stage2.
+cudaError_t launch_couple_rd(const StageArgs &s, bool f32, const double *Tm, double *Tout, cudaStream_t st);
 
 template <typename R> struct GeoTypes;
 template <> struct GeoTypes<double> { using Col = ColGeo; using Face = FaceGeo; };

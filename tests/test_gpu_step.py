@@ -203,3 +203,41 @@ def test_ppm_step_matches_oracle(name, n, level, prec, steps, C):
         assert rel_err(r["T_g"], r["T_o"]) < tol
     finally:
         r["gc"].close()
+
+
+RADDOM_CASES = [
+    # name, sizes, level, precision, recon, steps
+    ("turb3d", (7, 5, 6), 2, "f64", "plm", 2),          # flat, moving gas, rho spread over 1e-3 .. 10
+    ("turb3d", (7, 5, 6), 2, "f32", "plm", 2),
+    ("turb3d", (4, 3, 37), 2, "f64", "dc", 1),          # several chunks of cells along x3
+    ("torus3d", (8, 6, 4), 2, "f64", "plm", 2),         # Kerr-Schild, gas at rest, torus density x 10
+    ("torus3d_big", (6, 6, 4), 2, "f64", "dc", 1),      # moving gas and scattering in Kerr-Schild
+    ("torus3d_big", (6, 6, 4), 2, "f32", "plm", 1),
+]
+
+
+@pytest.mark.parametrize("name,n,level,prec,recon,steps", RADDOM_CASES)
+def test_radiation_dominated_substitution_matches_oracle(name, n, level, prec, recon, steps):
+    """The radiation-dominated velocity substitution (end of Sec. 2.5) against
+    the oracle: I and T to FP64 1e-12 / FP32 2e-5, the gas source to 1e-11
+    (FP64).  The density is spread so that the substitution is active in
+    some cells and not in others."""
+    from oracle import coupling as OC
+    from tests.harness import oracle_gas, oracle_setup
+    w = W.make(name, n=n, level=level)
+    if name == "turb3d":
+        w["rho"] = 10.0 ** np.random.default_rng(4).uniform(-3, 1, w["T"].shape)
+    else:
+        w["rho"] = 10.0 * w["rho"]       # a gas-dominated core inside a radiation-dominated envelope
+    st = oracle_setup(w)
+    act = OC.substituted_velocity(torch.tensor(w["I0"]), torch.tensor(w["T"]), oracle_gas(w), 0.01, st)[2]
+    assert 0 < int(act.sum()) < act.numel()
+    r = run_both(w, steps, prec, recon=recon, rad_dom=True)
+    try:
+        tol = TOL64 if prec == "f64" else TOL32
+        assert rel_err(r["I_g"], r["I_o"]) < tol
+        assert rel_err(r["T_g"], r["T_o"]) < tol
+        if prec == "f64":
+            assert rel_err(r["src_g"], r["src_o"]) < 1e-11
+    finally:
+        r["gc"].close()
