@@ -187,3 +187,79 @@ class GeodesicGrid:
 def boost_resolution(dOmega_max, v_max):
     """Smallest N_ang that keeps fluid-frame bins below dOmega_max (end of Sec. 2.6)."""
     return 4.0 * math.pi / dOmega_max * (1.0 + v_max) / (1.0 - v_max)
+
+
+class LatLongGrid:
+    """Latitude-longitude angle grid (Sec. 2.6).
+
+    N_zeta bands bounded by latitude lines equally spaced in cos(zeta) from
+    +1 to -1, and N_psi sectors bounded by longitude lines equally spaced in
+    psi from 0 to 2 pi: N_zeta N_psi cells of equal solid angle
+    4 pi / (N_zeta N_psi).  Readings (the paper states the grid only):
+      * the direction of a cell is the point halfway between its bounding
+        lines in cos(zeta) and in psi (it splits the cell into equal solid
+        angles both ways);
+      * the edges are the cell's sides: a meridian arc between two sectors
+        (a great-circle arc, length zeta_lo - zeta_hi, midpoint halfway in
+        zeta, normal e_psi) and a latitude arc between two bands (a small
+        circle, length sin(zeta_b) dpsi, midpoint at the sector's centre,
+        normal e_zeta); the polar caps are points and carry no flux;
+      * N_psi is even and at least 4, so that the pi rotation about the
+        2-axis maps cells to cells and no two cells share two sides.
+    Attributes as GeodesicGrid (n_ang, dir, dOmega, nbr, edges, edge_len,
+    edge_mid, edge_nrm, perm_pi2).
+    """
+
+    def __init__(self, n_zeta, n_psi):
+        if n_zeta < 1 or n_psi < 4 or n_psi % 2:
+            raise ValueError("lat/long grid needs N_zeta >= 1 and an even N_psi >= 4")
+        self.n_zeta, self.n_psi = n_zeta, n_psi
+        self.n_ang = n_zeta * n_psi
+        dpsi = 2.0 * math.pi / n_psi
+        cb = [1.0 - 2.0 * i / n_zeta for i in range(n_zeta + 1)]      # cos(zeta) of the latitude lines
+        zb = [math.acos(min(1.0, max(-1.0, c))) for c in cb]
+        cell = lambda i, j: i * n_psi + (j % n_psi)
+        dirs, dOm = [], []
+        for i in range(n_zeta):
+            cz = 0.5 * (cb[i] + cb[i + 1])
+            sz = math.sqrt(max(0.0, 1.0 - cz * cz))
+            for j in range(n_psi):
+                p = (j + 0.5) * dpsi
+                dirs.append((sz * math.cos(p), sz * math.sin(p), cz))
+                dOm.append((cb[i] - cb[i + 1]) * dpsi)
+        edges = []                      # (a, b, length, mid, normal from a to b)
+        for i in range(n_zeta):
+            zm = 0.5 * (zb[i] + zb[i + 1])
+            for j in range(n_psi):      # meridian at psi_b between sectors j and j + 1
+                pb = (j + 1) * dpsi
+                edges.append((cell(i, j), cell(i, j + 1), zb[i + 1] - zb[i],
+                               (math.sin(zm) * math.cos(pb), math.sin(zm) * math.sin(pb), math.cos(zm)),
+                               (-math.sin(pb), math.cos(pb), 0.0)))
+        for i in range(n_zeta - 1):     # latitude line between bands i and i + 1
+            z = zb[i + 1]
+            for j in range(n_psi):
+                pc = (j + 0.5) * dpsi
+                edges.append((cell(i, j), cell(i + 1, j), math.sin(z) * dpsi,
+                              (math.sin(z) * math.cos(pc), math.sin(z) * math.sin(pc), math.cos(z)),
+                              (math.cos(z) * math.cos(pc), math.cos(z) * math.sin(pc), -math.sin(z))))
+        pq, ln, mid, nrm = [], [], [], []
+        self.nbr = [[] for _ in range(self.n_ang)]
+        for a, b, length, m, nu in edges:
+            if a > b:                   # store p < q with the normal from p to q
+                a, b, nu = b, a, tuple(-x for x in nu)
+            pq.append((a, b))
+            ln.append(length)
+            mid.append(m)
+            nrm.append(nu)
+            self.nbr[a].append(b)
+            self.nbr[b].append(a)
+        self.dir = torch.tensor(dirs, dtype=DTYPE)
+        self.dOmega = torch.tensor(dOm, dtype=DTYPE)
+        self.edges = torch.tensor(pq, dtype=torch.long)
+        self.edge_len = torch.tensor(ln, dtype=DTYPE)
+        self.edge_mid = torch.tensor(mid, dtype=DTYPE)
+        self.edge_nrm = torch.tensor(nrm, dtype=DTYPE)
+        # (x, y, z) -> (-x, y, -z): zeta -> pi - zeta (band i -> N_zeta - 1 - i),
+        # psi -> pi - psi (sector j -> N_psi / 2 - 1 - j)
+        self.perm_pi2 = torch.tensor([cell(n_zeta - 1 - i, n_psi // 2 - 1 - j)
+                                      for i in range(n_zeta) for j in range(n_psi)], dtype=torch.long)

@@ -117,9 +117,9 @@ def test_plm_reproduces_linear_profile_slopes():
     assert torch.allclose(s, torch.tensor([0.3, -0.2, 0.0, 0.0], dtype=F64), atol=0, rtol=1e-15)
 
 
-def _hohlraum_error(level, ncell=64, t_end=0.5):
+def _hohlraum_error(level, ncell=64, t_end=0.5, ang=None):
     """1D hohlraum (Sec. 3.4): an isotropic wall of energy density 1 at x = 0."""
-    ang = GeodesicGrid(level)
+    ang = GeodesicGrid(level) if ang is None else ang
     xf = [np.linspace(0, 1, ncell + 1), np.array([0.0, 1.0]), np.array([0.0, 1.0])]
     grid = Grid("mink_cart", 0.0, xf, (("outflow", "outflow"),) * 3, 1)
     st = Setup(grid, ang)
@@ -157,6 +157,32 @@ def test_hohlraum_converges_in_angle():
     e = [_hohlraum_error(N) for N in (1, 2, 4)]
     assert e[0] > e[1] > e[2]
     assert e[2] < 0.03
+
+
+def test_hohlraum_converges_in_angle_on_latlong_grids():
+    """The same closed forms with latitude-longitude grids (Sec. 2.6) of
+    3 x 6, 6 x 12 and 12 x 24 angles."""
+    from oracle.angles import LatLongGrid
+    e = [_hohlraum_error(0, ang=LatLongGrid(nz, 2 * nz)) for nz in (3, 6, 12)]
+    assert e[0] > e[1] > e[2]
+    assert e[2] < 0.03
+
+
+def test_latlong_angular_fluxes_conserve_per_cell():
+    """Kerr-Schild with a latitude-longitude grid: the angular fluxes only
+    move intensity between bins of a cell."""
+    from oracle.angles import LatLongGrid
+    ang = LatLongGrid(4, 8)
+    xf = [np.exp(np.linspace(math.log(1.6), math.log(8.0), 7)), np.linspace(0, math.pi, 7),
+          np.linspace(0, 2 * math.pi, 5)]
+    grid = Grid("ks_sph", 0.9, xf, (("outflow", "outflow"), ("polar", "polar"), ("periodic", "periodic")), 3)
+    st = Setup(grid, ang)
+    rng = np.random.default_rng(4)
+    I = torch.tensor(rng.uniform(0.5, 1.5, grid.shape + (ang.n_ang,)))
+    divA = TR.angular_divergence(I, st)
+    tot = (divA * ang.dOmega).sum(-1)
+    assert tot.abs().max() < 1e-13 * float(divA.abs().max())
+    assert divA.abs().max() > 1e-3
 
 
 # ---------------------------------------------- optical-depth flux weighting
