@@ -4,7 +4,8 @@
  * The library advances the gray specific intensity I(x, n) of White et al.,
  * "General Relativistic Radiation with a Finite-Solid-Angle Method" (2023),
  * on one logically rectangular block of cells held on one GPU:
- *   - Sec. 2.6:      geodesic angle grid (rad_init_angles, rad_get_angles)
+ *   - Sec. 2.6:      geodesic and latitude-longitude angle grids
+ *                    (rad_init_angles, rad_init_angles_latlong, rad_get_angles)
  *   - Secs. 2.1-2.2: metric, normal-observer tetrad, Ricci rotation
  *                    coefficients, exact cell volumes (rad_set_metric)
  *   - Secs. 2.3-2.4, Eq. radiation_integral: reconstruction, upwind spatial
@@ -24,7 +25,7 @@
  *     never frees them.  The context owns its tables and scratch.
  *   - Streams: all device work is enqueued on the stream given to
  *     rad_create (NULL = legacy default stream).  Calls are asynchronous
- *     except rad_init_angles, rad_get_angles, rad_set_metric, rad_cfl_dt and
+ *     except rad_init_angles(_latlong), rad_get_angles, rad_set_metric, rad_cfl_dt and
  *     rad_check, which synchronise that stream.
  *   - Device errors (non-finite intensity, unbracketed quartic, divergent
  *     Newton iteration) set a sticky error word in device memory instead of
@@ -85,10 +86,27 @@ const char *rad_last_error(const rad_ctx *ctx);
 int rad_init_angles(rad_ctx *ctx, int level, int *n_ang_out, int *n_ang_padded_out);
 
 /*
+ * Latitude-longitude angle grid (Sec. 2.6) instead of the geodesic one:
+ * n_zeta bands between latitude lines equally spaced in cos(zeta) from +1
+ * to -1 (zeta measured from 3hat) and n_psi sectors between longitude lines
+ * equally spaced in psi from 0 to 2 pi, n_ang = n_zeta n_psi cells of solid
+ * angle 4 pi / n_ang.  Bin n = band * n_psi + sector; its direction lies
+ * halfway between its lines in cos(zeta) and in psi.  Angular fluxes cross
+ * the cell sides (meridian and latitude arcs, DC upwind as on the geodesic
+ * grid); the poles carry none.  n_psi must be even and >= 4 (the pi
+ * rotation about 2hat, used by polar boundaries, must map cells to cells),
+ * n_zeta >= 1, n_ang <= 4096 (rad_step takes up to 812): RAD_EINVAL
+ * otherwise.  Synchronous; invalidates the metric like rad_init_angles.
+ */
+int rad_init_angles_latlong(rad_ctx *ctx, int n_zeta, int n_psi, int *n_ang_out,
+                            int *n_ang_padded_out);
+
+/*
  * Copy the grid to host arrays (each may be NULL):
  *   dir[n_ang][3] unit directions (components on 1hat, 2hat, 3hat),
  *   dOmega[n_ang] exact spherical-polygon solid angles (sum 4 pi),
- *   nbr[n_ang][6] neighbour bins, -1 padding for the 12 pentagons.
+ *   nbr[n_ang][6] neighbour bins, -1 padding (the 12 pentagons of a
+ *                 geodesic grid, every cell of a lat/long grid).
  */
 int rad_get_angles(rad_ctx *ctx, double *dir, double *dOmega, int *nbr);
 

@@ -7,7 +7,7 @@ status codes and raises RadError with the library's message.  It never
 computes a result itself, and it refuses to run when librad.so is missing.
 
 Names match the C entry points: rad_create, rad_destroy, rad_init_angles,
-rad_get_angles, rad_set_metric, rad_cfl_dt, rad_step, rad_moments,
+rad_init_angles_latlong, rad_get_angles, rad_set_metric, rad_cfl_dt, rad_step, rad_moments,
 rad_step_adjoint, rad_loss_outer, rad_check, rad_opts_default.
 """
 import ctypes
@@ -83,6 +83,8 @@ def lib():
         "rad_last_error": ([_vp], ctypes.c_char_p),
         "rad_opts_default": ([P(rad_opts)], None),
         "rad_init_angles": ([_vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)], ctypes.c_int),
+        "rad_init_angles_latlong": ([_vp, ctypes.c_int, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)],
+                                    ctypes.c_int),
         "rad_get_angles": ([_vp, _vp, _vp, _vp], ctypes.c_int),
         "rad_set_metric": ([_vp, P(rad_metric), P(rad_grid)], ctypes.c_int),
         "rad_cfl_dt": ([_vp, ctypes.c_double, P(ctypes.c_double)], ctypes.c_int),
@@ -144,6 +146,12 @@ def rad_opts_default(**kw):
 def rad_init_angles(ctx, level):
     na, nap = ctypes.c_int(), ctypes.c_int()
     _check(ctx, lib().rad_init_angles(ctx, int(level), ctypes.byref(na), ctypes.byref(nap)))
+    return na.value, nap.value
+
+
+def rad_init_angles_latlong(ctx, n_zeta, n_psi):
+    na, nap = ctypes.c_int(), ctypes.c_int()
+    _check(ctx, lib().rad_init_angles_latlong(ctx, int(n_zeta), int(n_psi), ctypes.byref(na), ctypes.byref(nap)))
     return na.value, nap.value
 
 

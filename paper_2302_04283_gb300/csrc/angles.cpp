@@ -53,6 +53,32 @@ uint64_t lattice_key(std::array<std::pair<int, int>, 3> w) {
   return key;
 }
 
+// Bin of the direction rotated by pi about 2hat, (x, y, z) -> (-x, y, -z),
+// by nearest direction; fails unless the grid is symmetric under it.
+bool pi_rotation_perm(AngleGrid &g, std::string &err) {
+  const int n_ang = g.n_ang;
+  g.perm.assign(n_ang, -1);
+  for (int n = 0; n < n_ang; ++n) {
+    const double rx = -g.dir[3 * n], ry = g.dir[3 * n + 1], rz = -g.dir[3 * n + 2];
+    int best = -1;
+    double bd = 1e9;
+    for (int m = 0; m < n_ang; ++m) {
+      const double dx = rx - g.dir[3 * m], dy = ry - g.dir[3 * m + 1], dz = rz - g.dir[3 * m + 2];
+      const double dd = dx * dx + dy * dy + dz * dz;
+      if (dd < bd) {
+        bd = dd;
+        best = m;
+      }
+    }
+    if (bd > 1e-24) {
+      err = "angle grid is not symmetric under the pi rotation about 2hat";
+      return false;
+    }
+    g.perm[n] = best;
+  }
+  return true;
+}
+
 }  // namespace
 
 bool build_geodesic(int N, AngleGrid &g, std::string &err) {
@@ -206,27 +232,94 @@ bool build_geodesic(int N, AngleGrid &g, std::string &err) {
       g.slot_edge[6 * n + s] = nb[n][s].second;
     }
   }
-  // bin of the direction rotated by pi about 2hat: (x, y, z) -> (-x, y, -z)
-  g.perm.assign(n_ang, -1);
-  for (int n = 0; n < n_ang; ++n) {
-    V3 rd = {-dir[n].x, dir[n].y, -dir[n].z};
-    int best = -1;
-    double bd = 1e9;
-    for (int m = 0; m < n_ang; ++m) {
-      V3 d = sub(rd, dir[m]);
-      double dd = dot(d, d);
-      if (dd < bd) {
-        bd = dd;
-        best = m;
-      }
+  return pi_rotation_perm(g, err);
+}
+
+// Latitude-longitude grid (Sec. 2.6): n_zeta bands between latitude lines
+// equally spaced in cos(zeta) from +1 to -1, n_psi sectors between
+// longitude lines equally spaced in psi from 0 to 2 pi, every cell of solid
+// angle 4 pi / (n_zeta n_psi).  A cell's direction lies halfway between its
+// lines in cos(zeta) and in psi.  Its sides: meridian arcs to the
+// neighbouring sectors (great circles: length = the zeta extent, midpoint
+// halfway in zeta, normal e_psi) and latitude arcs to the neighbouring
+// bands (small circles: length sin(zeta) dpsi, midpoint at the sector's
+// centre, normal e_zeta); the poles are points and carry no flux.  Cell
+// index n = band * n_psi + sector.
+bool build_latlong(int n_zeta, int n_psi, AngleGrid &g, std::string &err) {
+  if (n_zeta < 1 || n_psi < 4 || (n_psi & 1) || (long long)n_zeta * n_psi > 4096) {
+    err = "lat/long grid needs n_zeta >= 1, an even n_psi >= 4 and at most 4096 cells";
+    return false;
+  }
+  g = AngleGrid();
+  g.level = 0;
+  g.n_ang = n_zeta * n_psi;
+  g.n_ap = (g.n_ang + 3) / 4 * 4;
+  const double dpsi = 2.0 * kPi / n_psi;
+  std::vector<double> cz(n_zeta + 1), zl(n_zeta + 1);
+  for (int i = 0; i <= n_zeta; ++i) {
+    cz[i] = 1.0 - 2.0 * i / n_zeta;
+    zl[i] = std::acos(std::min(1.0, std::max(-1.0, cz[i])));
+  }
+  g.dir.resize(3 * g.n_ang);
+  g.dOmega.resize(g.n_ang);
+  for (int i = 0; i < n_zeta; ++i) {
+    const double c = 0.5 * (cz[i] + cz[i + 1]), sn = std::sqrt(std::max(0.0, 1.0 - c * c));
+    for (int j = 0; j < n_psi; ++j) {
+      const int n = i * n_psi + j;
+      const double p = (j + 0.5) * dpsi;
+      g.dir[3 * n] = sn * std::cos(p);
+      g.dir[3 * n + 1] = sn * std::sin(p);
+      g.dir[3 * n + 2] = c;
+      g.dOmega[n] = (cz[i] - cz[i + 1]) * dpsi;
     }
-    if (bd > 1e-24) {
-      err = "angle grid is not symmetric under the pi rotation about 2hat";
+  }
+  std::vector<std::vector<std::pair<int, int>>> nb(g.n_ang);
+  auto add_edge = [&](int a, int b, double len, V3 mid, V3 nu) {
+    if (a > b) {
+      std::swap(a, b);
+      nu = mul(nu, -1.0);
+    }
+    const int e = g.n_edge++;
+    g.edge_pq.push_back(a);
+    g.edge_pq.push_back(b);
+    g.edge_mid.insert(g.edge_mid.end(), {mid.x, mid.y, mid.z});
+    g.edge_nrm.insert(g.edge_nrm.end(), {nu.x, nu.y, nu.z});
+    g.edge_len.push_back(len);
+    nb[a].push_back({b, e});
+    nb[b].push_back({a, e});
+  };
+  for (int i = 0; i < n_zeta; ++i) {
+    const double zm = 0.5 * (zl[i] + zl[i + 1]);
+    for (int j = 0; j < n_psi; ++j) {            // meridian between sectors j and j + 1
+      const double pb = (j + 1) * dpsi;
+      add_edge(i * n_psi + j, i * n_psi + (j + 1) % n_psi, zl[i + 1] - zl[i],
+               V3{std::sin(zm) * std::cos(pb), std::sin(zm) * std::sin(pb), std::cos(zm)},
+               V3{-std::sin(pb), std::cos(pb), 0.0});
+    }
+  }
+  for (int i = 0; i + 1 < n_zeta; ++i) {
+    const double z = zl[i + 1];
+    for (int j = 0; j < n_psi; ++j) {            // latitude line between bands i and i + 1
+      const double pc = (j + 0.5) * dpsi;
+      add_edge(i * n_psi + j, (i + 1) * n_psi + j, std::sin(z) * dpsi,
+               V3{std::sin(z) * std::cos(pc), std::sin(z) * std::sin(pc), std::cos(z)},
+               V3{std::cos(z) * std::cos(pc), std::cos(z) * std::sin(pc), -std::sin(z)});
+    }
+  }
+  g.nbr.assign(6 * g.n_ang, -1);
+  g.slot_edge.assign(6 * g.n_ang, -1);
+  for (int n = 0; n < g.n_ang; ++n) {
+    std::sort(nb[n].begin(), nb[n].end());
+    if (nb[n].size() > 6) {
+      err = "lat/long cell with more than six sides";
       return false;
     }
-    g.perm[n] = best;
+    for (size_t s = 0; s < nb[n].size(); ++s) {
+      g.nbr[6 * n + s] = nb[n][s].first;
+      g.slot_edge[6 * n + s] = nb[n][s].second;
+    }
   }
-  return true;
+  return pi_rotation_perm(g, err);
 }
 
 }  // namespace rad

@@ -95,11 +95,9 @@ void rad_opts_default(rad_opts *o) {
   o->rad_dom = 0;
 }
 
-int rad_init_angles(rad_ctx *ctx, int level, int *n_ang_out, int *n_ang_padded_out) {
-  if (!ctx) return RAD_EINVAL;
-  AngleGrid g;
-  std::string err;
-  if (!rad::build_geodesic(level, g, err)) return fail(ctx, RAD_EINVAL, err);
+// Upload a built angle grid and make it the context's (the metric must be
+// set again afterwards).
+static int install_angles(rad_ctx *ctx, AngleGrid &g, int *n_ang_out, int *n_ang_padded_out) {
   cudaStreamSynchronize(ctx->stream);
   free_angles(ctx->dang);
   cudaFree(ctx->wt_dev);
@@ -143,6 +141,22 @@ int rad_init_angles(rad_ctx *ctx, int level, int *n_ang_out, int *n_ang_padded_o
   if (n_ang_out) *n_ang_out = ctx->ang.n_ang;
   if (n_ang_padded_out) *n_ang_padded_out = ctx->ang.n_ap;
   return RAD_OK;
+}
+
+int rad_init_angles(rad_ctx *ctx, int level, int *n_ang_out, int *n_ang_padded_out) {
+  if (!ctx) return RAD_EINVAL;
+  AngleGrid g;
+  std::string err;
+  if (!rad::build_geodesic(level, g, err)) return fail(ctx, RAD_EINVAL, err);
+  return install_angles(ctx, g, n_ang_out, n_ang_padded_out);
+}
+
+int rad_init_angles_latlong(rad_ctx *ctx, int n_zeta, int n_psi, int *n_ang_out, int *n_ang_padded_out) {
+  if (!ctx) return RAD_EINVAL;
+  AngleGrid g;
+  std::string err;
+  if (!rad::build_latlong(n_zeta, n_psi, g, err)) return fail(ctx, RAD_EINVAL, err);
+  return install_angles(ctx, g, n_ang_out, n_ang_padded_out);
 }
 
 int rad_get_angles(rad_ctx *ctx, double *dir, double *dOmega, int *nbr) {
@@ -266,8 +280,8 @@ int rad_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opt
   if ((st = check_gas(ctx, gas, o, true)) != RAD_OK) return st;
   if (!I || !aligned16(I)) return fail(ctx, RAD_EINVAL, "I must be a 16-byte aligned device pointer");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, RAD_EINVAL, "dt must be finite and > 0");
-  if (ctx->ang.level > rad::kMaxLevelStep)
-    return fail(ctx, RAD_EUNSUPPORTED, "rad_step supports geodesic levels up to 9");
+  if (ctx->ang.n_ang > rad::kMaxBinsStep)
+    return fail(ctx, RAD_EUNSUPPORTED, "rad_step supports up to 812 bins (geodesic level 9)");
   const rad::DevGeom &G = ctx->geom;
   size_t ncell = (size_t)G.n[0] * G.n[1] * G.n[2];
   size_t esz = o->precision == RAD_F32 ? 4 : 8;
@@ -328,8 +342,8 @@ int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double d
     return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers the coupling at the gas velocity (rad_dom = 0)");
   if (!I_n || !lam_np1 || !lam_n || !g_aa || !g_as) return fail(ctx, RAD_EINVAL, "null argument");
   if (!(dt > 0.0)) return fail(ctx, RAD_EINVAL, "dt must be > 0");
-  if (ctx->ang.level > rad::kMaxLevelStep)
-    return fail(ctx, RAD_EUNSUPPORTED, "rad_step_adjoint supports geodesic levels up to 9");
+  if (ctx->ang.n_ang > rad::kMaxBinsStep)
+    return fail(ctx, RAD_EUNSUPPORTED, "rad_step_adjoint supports up to 812 bins (geodesic level 9)");
   std::string err;
   st = rad::launch_adjoint(ctx, I_n, gas, dt, o, lam_np1, lam_n, lamT_np1, lamT_n, g_aa, g_as, g_eta, err);
   return st == RAD_OK ? st : fail(ctx, st, err);

@@ -82,8 +82,8 @@ extern "C" int rad_step_noalloc(rad_ctx *ctx, void *I, const rad_gas *gas, doubl
   if (!gas->T) return fail(ctx, RAD_EINVAL, "gas->T is required");
   if (!I || ((uintptr_t)I & 15u)) return fail(ctx, RAD_EINVAL, "I must be a 16-byte aligned device pointer");
   if (!(dt > 0.0) || !(dt < 1e300)) return fail(ctx, RAD_EINVAL, "dt must be finite and > 0");
-  if (ctx->ang.level > rad::kMaxLevelStep)
-    return fail(ctx, RAD_EUNSUPPORTED, "rad_step_noalloc supports geodesic levels up to 9");
+  if (ctx->ang.n_ang > rad::kMaxBinsStep)
+    return fail(ctx, RAD_EUNSUPPORTED, "rad_step_noalloc supports up to 812 bins (geodesic level 9)");
   const rad::DevGeom &G = ctx->geom;
   const size_t ncell = (size_t)G.n[0] * G.n[1] * G.n[2];
   const size_t esz = o->precision == RAD_F32 ? 4 : 8;

@@ -12,7 +12,8 @@
 namespace rad {
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr int kMaxLevelStep = 9;         // rad_step: one CTA of <= 512 threads holds all bins of a cell
+constexpr int kMaxBinsStep = 812;        // rad_step: one CTA of <= 512 threads holds all bins of a cell
+                                         // (812 = geodesic level 9)
 constexpr int kMaxSlots = 6;             // neighbours of a geodesic cell
 
 // error bits of the sticky device word (bit k <-> status -k)
@@ -34,6 +35,7 @@ struct AngleGrid {
 };
 
 bool build_geodesic(int level, AngleGrid &g, std::string &err);
+bool build_latlong(int n_zeta, int n_psi, AngleGrid &g, std::string &err);
 
 // Per-cell geometry of one (i, j) column (the metrics are x3-independent).
 struct ColGeo {

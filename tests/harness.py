@@ -10,16 +10,16 @@ import paper_2302_04283_gb300 as rad
 import workloads as W
 from oracle import cfl as OCFL
 from oracle import step as OS
-from oracle.angles import GeodesicGrid
+from oracle.angles import GeodesicGrid, LatLongGrid
 from oracle.transport import Grid, Setup
 
 _SETUPS = {}
 
 
 def oracle_setup(w):
-    key = (w["name"], w["n"], w["level"], w["kind"], w["spin"])
+    key = (w["name"], w["n"], w["level"], w["kind"], w["spin"], w.get("latlong"))
     if key not in _SETUPS:
-        ang = GeodesicGrid(w["level"])
+        ang = GeodesicGrid(w["level"]) if w.get("latlong") is None else LatLongGrid(*w["latlong"])
         _SETUPS[key] = Setup(Grid(w["kind"], w["spin"], w["xf"], w["bc"], w["ndim"]), ang)
     return _SETUPS[key]
 
@@ -41,7 +41,10 @@ class GpuCase:
         self.dev = dev
         self.stream = torch.cuda.current_stream()
         self.ctx = rad.rad_create(self.stream)
-        self.n_ang, self.n_ap = rad.rad_init_angles(self.ctx, w["level"])
+        if w.get("latlong") is None:
+            self.n_ang, self.n_ap = rad.rad_init_angles(self.ctx, w["level"])
+        else:
+            self.n_ang, self.n_ap = rad.rad_init_angles_latlong(self.ctx, *w["latlong"])
         self.dir, self.dOmega, self.nbr = rad.rad_get_angles(self.ctx, self.n_ang)
         rad.rad_set_metric(self.ctx, w["kind"], w["spin"], w["ndim"], w["xf"], w["bc"])
 

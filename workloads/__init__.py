@@ -92,7 +92,7 @@ def torus_density(r, th):
     return np.exp(-((r - 10.0) ** 2 + (10.0 * np.cos(th)) ** 2) / 8.0) + 1e-4
 
 
-def make(name, n=None, level=None, seed=None, with_intensity=True):
+def make(name, n=None, level=None, seed=None, with_intensity=True, latlong=None):
     """Return a dict describing one workload (all float64 numpy arrays).
 
     keys: kind, spin, xf (3 face arrays), bc, ndim, level, nsteps, cfl, mode,
@@ -134,6 +134,9 @@ def make(name, n=None, level=None, seed=None, with_intensity=True):
     else:
         raise ValueError(name)
     w["level"], w["seed"], w["n"] = level, seed, tuple(n)
+    # angle grid: the geodesic grid of the level, or a (n_zeta, n_psi)
+    # latitude-longitude grid in its place
+    w["latlong"] = tuple(latlong) if latlong is not None else None
     rng = np.random.Generator(np.random.PCG64(seed))
     xc = [_centres(x) for x in w["xf"]]
     shape = (n[2], n[1], n[0])
@@ -176,7 +179,7 @@ def make(name, n=None, level=None, seed=None, with_intensity=True):
         w["alpha_s"] = (10.0 ** fs)[None].copy()
         w["eta"] = ((10.0 ** fe) / (4 * math.pi))[None].copy()
     if with_intensity:
-        na = n_ang(level)
+        na = n_ang(level) if latlong is None else latlong[0] * latlong[1]
         U = rng.uniform(-1.0, 1.0, shape + (na,))
         if name == "adjoint2d":
             base = np.full(shape, 1.0 / (4 * math.pi))
