@@ -106,6 +106,19 @@ __device__ __forceinline__ float rcp_approx(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+// FP64 reciprocal: the hardware approximation refined by two Newton-Raphson
+// steps for f(r) = 1/r - x (r <- r + r (1 - x r), quadratic convergence), a
+// few ulp from 1/x: cheaper on the FP64 pipe than a correctly rounded
+// division, and far inside the FP64 path's 1e-12 tolerance.  x = 0 gives a
+// non-finite result (as 1/x does); callers discard it.
+__device__ __forceinline__ double rcp_newton(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
 
 // PLM half-slope q = dl dr / (dl + dr) if dl dr > 0 else 0 (van Leer 1974).
 template <typename R>
@@ -243,7 +256,7 @@ template <> struct P2<double> {
   static __device__ __forceinline__ V sub(V a, V b) { return make_double2(a.x - b.x, a.y - b.y); }
   static __device__ __forceinline__ V mul(V a, V b) { return make_double2(a.x * b.x, a.y * b.y); }
   static __device__ __forceinline__ V fma(V a, V b, V c) { return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
-  static __device__ __forceinline__ V rcp(V a) { return make_double2(1.0 / a.x, 1.0 / a.y); }
+  static __device__ __forceinline__ V rcp(V a) { return make_double2(rcp_newton(a.x), rcp_newton(a.y)); }
 };
 
 // van Leer half-slopes of a pair: q = dl dr / (dl + dr) if dl dr > 0, else 0.
@@ -255,13 +268,8 @@ __device__ __forceinline__ typename P2<R>::V vl2(typename P2<R>::V x, typename P
   auto s = P::add(dl, dr);
   // both quotients are formed unconditionally and the select discards the
   // ones of non-positive products (including 0/0), so no branch is taken
-  if constexpr (sizeof(R) == 4) {
-    const auto q = P::mul(prod, P::rcp(s));                    // one packed multiply
-    return P::mk(prod.x > R(0) ? q.x : R(0), prod.y > R(0) ? q.y : R(0));
-  } else {
-    const R qx = fdiv(prod.x, s.x), qy = fdiv(prod.y, s.y);
-    return P::mk(prod.x > R(0) ? qx : R(0), prod.y > R(0) ? qy : R(0));
-  }
+  const auto q = P::mul(prod, P::rcp(s));                      // one (packed) multiply by reciprocals
+  return P::mk(prod.x > R(0) ? q.x : R(0), prod.y > R(0) ? q.y : R(0));
 }
 
 template <typename R>
