@@ -207,7 +207,15 @@ class LatLongGrid:
       * N_psi is even and at least 4, so that the pi rotation about the
         2-axis maps cells to cells and no two cells share two sides.
     Attributes as GeodesicGrid (n_ang, dir, dOmega, nbr, edges, edge_len,
-    edge_mid, edge_nrm, perm_pi2).
+    edge_mid, edge_nrm, perm_pi2), plus
+      edge_line  [n_edge, 2]  for the side between p and q: the cell behind p
+                              and the cell beyond q on the line through p and
+                              q (a band for a meridian side; a sector for a
+                              latitude side, continued across a pole into
+                              the sector psi + pi of the same band), for
+                              reconstruction along the line (Sec. 2.6 reads
+                              "the same algorithms as spatial
+                              reconstruction": PLM across the poles).
     """
 
     def __init__(self, n_zeta, n_psi):
@@ -219,6 +227,14 @@ class LatLongGrid:
         cb = [1.0 - 2.0 * i / n_zeta for i in range(n_zeta + 1)]      # cos(zeta) of the latitude lines
         zb = [math.acos(min(1.0, max(-1.0, c))) for c in cb]
         cell = lambda i, j: i * n_psi + (j % n_psi)
+
+        def zeta_line(i, j):
+            """Cell i of the line of sector j through both poles (i may be -1 or n_zeta)."""
+            if i < 0:
+                return cell(0, j + n_psi // 2)
+            if i >= n_zeta:
+                return cell(n_zeta - 1, j + n_psi // 2)
+            return cell(i, j)
         dirs, dOm = [], []
         for i in range(n_zeta):
             cz = 0.5 * (cb[i] + cb[i + 1])
@@ -227,27 +243,30 @@ class LatLongGrid:
                 p = (j + 0.5) * dpsi
                 dirs.append((sz * math.cos(p), sz * math.sin(p), cz))
                 dOm.append((cb[i] - cb[i + 1]) * dpsi)
-        edges = []                      # (a, b, length, mid, normal from a to b)
+        edges = []                      # (a, b, length, mid, normal from a to b, behind a, beyond b)
         for i in range(n_zeta):
             zm = 0.5 * (zb[i] + zb[i + 1])
             for j in range(n_psi):      # meridian at psi_b between sectors j and j + 1
                 pb = (j + 1) * dpsi
                 edges.append((cell(i, j), cell(i, j + 1), zb[i + 1] - zb[i],
                                (math.sin(zm) * math.cos(pb), math.sin(zm) * math.sin(pb), math.cos(zm)),
-                               (-math.sin(pb), math.cos(pb), 0.0)))
+                               (-math.sin(pb), math.cos(pb), 0.0), cell(i, j - 1), cell(i, j + 2)))
         for i in range(n_zeta - 1):     # latitude line between bands i and i + 1
             z = zb[i + 1]
             for j in range(n_psi):
                 pc = (j + 0.5) * dpsi
                 edges.append((cell(i, j), cell(i + 1, j), math.sin(z) * dpsi,
                               (math.sin(z) * math.cos(pc), math.sin(z) * math.sin(pc), math.cos(z)),
-                              (math.cos(z) * math.cos(pc), math.cos(z) * math.sin(pc), -math.sin(z))))
-        pq, ln, mid, nrm = [], [], [], []
+                              (math.cos(z) * math.cos(pc), math.cos(z) * math.sin(pc), -math.sin(z)),
+                              zeta_line(i - 1, j), zeta_line(i + 2, j)))
+        pq, ln, mid, nrm, line = [], [], [], [], []
         self.nbr = [[] for _ in range(self.n_ang)]
-        for a, b, length, m, nu in edges:
+        for a, b, length, m, nu, behind, beyond in edges:
             if a > b:                   # store p < q with the normal from p to q
                 a, b, nu = b, a, tuple(-x for x in nu)
+                behind, beyond = beyond, behind
             pq.append((a, b))
+            line.append((behind, beyond))
             ln.append(length)
             mid.append(m)
             nrm.append(nu)
@@ -259,6 +278,7 @@ class LatLongGrid:
         self.edge_len = torch.tensor(ln, dtype=DTYPE)
         self.edge_mid = torch.tensor(mid, dtype=DTYPE)
         self.edge_nrm = torch.tensor(nrm, dtype=DTYPE)
+        self.edge_line = torch.tensor(line, dtype=torch.long)
         # (x, y, z) -> (-x, y, -z): zeta -> pi - zeta (band i -> N_zeta - 1 - i),
         # psi -> pi - psi (sector j -> N_psi / 2 - 1 - j)
         self.perm_pi2 = torch.tensor([cell(n_zeta - 1 - i, n_psi // 2 - 1 - j)

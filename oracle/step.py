@@ -35,13 +35,14 @@ class Opts:
     couple: bool = True
     tau_const: float = 0.0      # C of the optical-depth flux weighting (0: free streaming)
     rad_dom: bool = False       # radiation-dominated velocity substitution (Sec. 2.5)
+    recon_ang: str = "dc"       # 'dc' | 'plm' (PLM along the lines of a latitude-longitude grid)
 
 
 def operator_L(I, setup, opts, tau=None):
     """L(I) = -(div_space + div_angle), Eq. radiation_integral without sources."""
     Ie = TR.fill_ghosts(I, setup.grid, setup.ang.perm_pi2)
     divS = TR.spatial_divergence(Ie, setup, opts.recon, tau)
-    divA = TR.angular_divergence(I, setup)
+    divA = TR.angular_divergence(I, setup, opts.recon_ang)
     return -(divS + divA)
 
 

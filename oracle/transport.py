@@ -365,13 +365,30 @@ def angular_speeds(setup):
     return ang.edge_len * s * n0, s
 
 
-def angular_divergence(I, setup):
-    """(1/dOmega_p) sum over the edges of p of the outgoing DC-upwind flux."""
+def angular_face_values(I, ang, recon_ang="dc"):
+    """Upwind candidates at every side p | q: (value from p, value from q).
+
+    DC: the cell values.  PLM (latitude-longitude grids, Sec. 2.6): the
+    spatial reconstruction applied along the line through p and q, i.e.
+    I_p + van_leer(I_p - I_behind, I_q - I_p) / 2 from p and
+    I_q + van_leer(I_q - I_beyond, I_p - I_q) / 2 from q."""
+    p, q = ang.edges[:, 0], ang.edges[:, 1]
+    Ip, Iq = I[..., p], I[..., q]
+    if recon_ang == "dc":
+        return Ip, Iq
+    if recon_ang != "plm" or not hasattr(ang, "edge_line"):
+        raise ValueError("angular PLM needs a latitude-longitude grid")
+    Ib, If = I[..., ang.edge_line[:, 0]], I[..., ang.edge_line[:, 1]]
+    return Ip + 0.5 * van_leer(Ip - Ib, Iq - Ip), Iq + 0.5 * van_leer(Iq - If, Ip - Iq)
+
+
+def angular_divergence(I, setup, recon_ang="dc"):
+    """(1/dOmega_p) sum over the edges of p of the outgoing upwind flux."""
     ang = setup.ang
     coef, s = angular_speeds(setup)
     p, q = ang.edges[:, 0], ang.edges[:, 1]
-    Ip, Iq = I[..., p], I[..., q]
-    F = coef * torch.where(s < 0.0, Iq, Ip)            # tie -> p side
+    Fp, Fq = angular_face_values(I, ang, recon_ang)
+    F = coef * torch.where(s < 0.0, Fq, Fp)            # tie -> p side
     div = torch.zeros_like(I)
     div = div.index_add(-1, p, F / ang.dOmega[p])
     div = div.index_add(-1, q, -F / ang.dOmega[q])

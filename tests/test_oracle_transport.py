@@ -168,9 +168,10 @@ def test_hohlraum_converges_in_angle_on_latlong_grids():
     assert e[2] < 0.03
 
 
-def test_latlong_angular_fluxes_conserve_per_cell():
+@pytest.mark.parametrize("recon_ang", ["dc", "plm"])
+def test_latlong_angular_fluxes_conserve_per_cell(recon_ang):
     """Kerr-Schild with a latitude-longitude grid: the angular fluxes only
-    move intensity between bins of a cell."""
+    move intensity between bins of a cell (DC and PLM along the grid lines)."""
     from oracle.angles import LatLongGrid
     ang = LatLongGrid(4, 8)
     xf = [np.exp(np.linspace(math.log(1.6), math.log(8.0), 7)), np.linspace(0, math.pi, 7),
@@ -179,7 +180,7 @@ def test_latlong_angular_fluxes_conserve_per_cell():
     st = Setup(grid, ang)
     rng = np.random.default_rng(4)
     I = torch.tensor(rng.uniform(0.5, 1.5, grid.shape + (ang.n_ang,)))
-    divA = TR.angular_divergence(I, st)
+    divA = TR.angular_divergence(I, st, recon_ang)
     tot = (divA * ang.dOmega).sum(-1)
     assert tot.abs().max() < 1e-13 * float(divA.abs().max())
     assert divA.abs().max() > 1e-3
