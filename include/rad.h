@@ -174,6 +174,13 @@ typedef struct {
                         Needs RAD_COUPLE_THERMAL; each stage then runs the
                         transport and the coupling as two kernels.  Default 0;
                         rad_step_adjoint requires 0. */
+  int recon_ang;     /* angular reconstruction: RAD_RECON_DC (default; the
+                        geodesic grid's scheme, Sec. 2.6) or RAD_RECON_PLM:
+                        the spatial PLM applied along the lines of a
+                        latitude-longitude grid (bands along a side of
+                        constant psi, sectors through both poles for a
+                        side of constant zeta; RAD_EUNSUPPORTED on a
+                        geodesic grid).  rad_step_adjoint requires DC. */
 } rad_opts;
 
 /* Fill *opts with the defaults above (FP64, PLM, thermal coupling). */

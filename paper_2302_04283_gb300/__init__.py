@@ -56,7 +56,8 @@ class rad_host_item(ctypes.Structure):
 class rad_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("recon", ctypes.c_int), ("coupling", ctypes.c_int),
                 ("n0crit", ctypes.c_double), ("zero_guard", ctypes.c_int), ("a_rad", ctypes.c_double),
-                ("gamma", ctypes.c_double), ("tau_const", ctypes.c_double), ("rad_dom", ctypes.c_int)]
+                ("gamma", ctypes.c_double), ("tau_const", ctypes.c_double), ("rad_dom", ctypes.c_int),
+                ("recon_ang", ctypes.c_int)]
 
 
 class RadError(RuntimeError):

@@ -14,7 +14,7 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
 
 SOURCES = ["angles.cpp", "capi.cu", "geom.cu", "step.cu", "stage_f32_flat.cu", "stage_f32_ang.cu",
-           "stage_f64_flat.cu", "stage_f64_ang.cu", "moments.cu", "moments_tc.cu", "adjoint.cu", "noalloc.cu",
+           "stage_f64_flat.cu", "stage_f64_ang.cu", "stage_f32_angplm.cu", "stage_f64_angplm.cu", "moments.cu", "moments_tc.cu", "adjoint.cu", "noalloc.cu",
            "host_stream.cu", "raddom.cu"]
 
 

@@ -274,14 +274,26 @@ bool build_latlong(int n_zeta, int n_psi, AngleGrid &g, std::string &err) {
     }
   }
   std::vector<std::vector<std::pair<int, int>>> nb(g.n_ang);
-  auto add_edge = [&](int a, int b, double len, V3 mid, V3 nu) {
+  // the cell at band i of the line of sector j through both poles (i = -1
+  // or n_zeta continues across the pole into sector j + n_psi / 2)
+  auto zeta_line = [&](int i, int j) {
+    if (i < 0) return (j + n_psi / 2) % n_psi;
+    if (i >= n_zeta) return (n_zeta - 1) * n_psi + (j + n_psi / 2) % n_psi;
+    return i * n_psi + j;
+  };
+  // side between cells a and b; behind = the cell before a, beyond = the cell
+  // after b on the line through them (for reconstruction along the line)
+  auto add_edge = [&](int a, int b, double len, V3 mid, V3 nu, int behind, int beyond) {
     if (a > b) {
       std::swap(a, b);
+      std::swap(behind, beyond);
       nu = mul(nu, -1.0);
     }
     const int e = g.n_edge++;
     g.edge_pq.push_back(a);
     g.edge_pq.push_back(b);
+    g.edge_line.push_back(behind);
+    g.edge_line.push_back(beyond);
     g.edge_mid.insert(g.edge_mid.end(), {mid.x, mid.y, mid.z});
     g.edge_nrm.insert(g.edge_nrm.end(), {nu.x, nu.y, nu.z});
     g.edge_len.push_back(len);
@@ -294,7 +306,8 @@ bool build_latlong(int n_zeta, int n_psi, AngleGrid &g, std::string &err) {
       const double pb = (j + 1) * dpsi;
       add_edge(i * n_psi + j, i * n_psi + (j + 1) % n_psi, zl[i + 1] - zl[i],
                V3{std::sin(zm) * std::cos(pb), std::sin(zm) * std::sin(pb), std::cos(zm)},
-               V3{-std::sin(pb), std::cos(pb), 0.0});
+               V3{-std::sin(pb), std::cos(pb), 0.0}, i * n_psi + (j + n_psi - 1) % n_psi,
+               i * n_psi + (j + 2) % n_psi);
     }
   }
   for (int i = 0; i + 1 < n_zeta; ++i) {
@@ -303,7 +316,8 @@ bool build_latlong(int n_zeta, int n_psi, AngleGrid &g, std::string &err) {
       const double pc = (j + 0.5) * dpsi;
       add_edge(i * n_psi + j, (i + 1) * n_psi + j, std::sin(z) * dpsi,
                V3{std::sin(z) * std::cos(pc), std::sin(z) * std::sin(pc), std::cos(z)},
-               V3{std::cos(z) * std::cos(pc), std::cos(z) * std::sin(pc), -std::sin(z)});
+               V3{std::cos(z) * std::cos(pc), std::cos(z) * std::sin(pc), -std::sin(z)}, zeta_line(i - 1, j),
+               zeta_line(i + 2, j));
     }
   }
   g.nbr.assign(6 * g.n_ang, -1);

@@ -23,6 +23,7 @@ void free_angles(rad::DevAngles &d) {
   cudaFree(d.perm);
   cudaFree(d.edge_geo);
   cudaFree(d.edge_pq);
+  cudaFree(d.edge_line);
   d = rad::DevAngles();
 }
 
@@ -93,6 +94,7 @@ void rad_opts_default(rad_opts *o) {
   o->gamma = 5.0 / 3.0;
   o->tau_const = 0.0;
   o->rad_dom = 0;
+  o->recon_ang = RAD_RECON_DC;
 }
 
 // Upload a built angle grid and make it the context's (the metric must be
@@ -130,7 +132,8 @@ static int install_angles(rad_ctx *ctx, AngleGrid &g, int *n_ang_out, int *n_ang
       (ce = upload(&ctx->dang.slot_edge, sed, ctx->stream)) != cudaSuccess ||
       (ce = upload(&ctx->dang.perm, perm, ctx->stream)) != cudaSuccess ||
       (ce = upload(&ctx->dang.edge_geo, egeo, ctx->stream)) != cudaSuccess ||
-      (ce = upload(&ctx->dang.edge_pq, g.edge_pq, ctx->stream)) != cudaSuccess) {
+      (ce = upload(&ctx->dang.edge_pq, g.edge_pq, ctx->stream)) != cudaSuccess ||
+      (!g.edge_line.empty() && (ce = upload(&ctx->dang.edge_line, g.edge_line, ctx->stream)) != cudaSuccess)) {
     free_angles(ctx->dang);
     return fail(ctx, RAD_ENOMEM, std::string("angle table upload failed: ") + cudaGetErrorString(ce));
   }
@@ -267,6 +270,9 @@ static int check_opts(rad_ctx *ctx, const rad_opts *o) {
   if (!(o->tau_const >= 0.0) || !std::isfinite(o->tau_const))
     return fail(ctx, RAD_EINVAL, "tau_const must be finite and >= 0");
   if (o->rad_dom != 0 && o->rad_dom != 1) return fail(ctx, RAD_EINVAL, "rad_dom must be 0 or 1");
+  if (o->recon_ang != RAD_RECON_DC && o->recon_ang != RAD_RECON_PLM) return fail(ctx, RAD_EINVAL, "bad recon_ang");
+  if (o->recon_ang == RAD_RECON_PLM && ctx->ang.edge_line.empty())
+    return fail(ctx, RAD_EUNSUPPORTED, "angular PLM needs a latitude-longitude grid (rad_init_angles_latlong)");
   if (o->rad_dom && o->coupling != RAD_COUPLE_THERMAL)
     return fail(ctx, RAD_EINVAL, "rad_dom applies to the thermal coupling");
   return RAD_OK;
@@ -340,6 +346,8 @@ int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double d
     return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers DC and PLM reconstruction");
   if (o->rad_dom)
     return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers the coupling at the gas velocity (rad_dom = 0)");
+  if (o->recon_ang != RAD_RECON_DC)
+    return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers donor-cell angular fluxes (recon_ang = RAD_RECON_DC)");
   if (!I_n || !lam_np1 || !lam_n || !g_aa || !g_as) return fail(ctx, RAD_EINVAL, "null argument");
   if (!(dt > 0.0)) return fail(ctx, RAD_EINVAL, "dt must be > 0");
   if (ctx->ang.n_ang > rad::kMaxBinsStep)

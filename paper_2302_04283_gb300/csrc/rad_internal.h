@@ -32,6 +32,8 @@ struct AngleGrid {
   std::vector<double> edge_len;   // [n_edge]
   std::vector<int> slot_edge;     // [n_ang][6] edge id of each neighbour slot (-1 pad)
   std::vector<int> perm;          // [n_ang] bin of the pi-rotation about 2hat
+  std::vector<int> edge_line;     // [n_edge][2] cell behind p, cell beyond q on the line through the
+                                  // side (latitude-longitude grids; empty for the geodesic grid)
 };
 
 bool build_geodesic(int level, AngleGrid &g, std::string &err);
@@ -79,6 +81,7 @@ struct DevAngles {
   int *perm = nullptr;         // [n_ap]
   double *edge_geo = nullptr;  // [n_edge][8]: mid xyz, nrm xyz, len, p-index
   int *edge_pq = nullptr;      // [n_edge][2]
+  int *edge_line = nullptr;    // [n_edge][2] (latitude-longitude grids only)
 };
 
 struct DevGeom {

@@ -1,0 +1,9 @@
+// F64 stage kernels with angular fluxes and PLM angular reconstruction
+// along the lines of a latitude-longitude grid.
+#include "stage_launch.cuh"
+
+namespace rad {
+
+template cudaError_t launch_stage_rp<double, true, true>(const StageArgs &a, cudaStream_t st);
+
+}  // namespace rad

@@ -8,10 +8,10 @@
 
 namespace rad {
 
-template <typename R, bool ANG, int RC, bool ST2, bool TAU>
+template <typename R, bool ANG, int RC, bool ST2, bool TAU, bool AP>
 cudaError_t launch_stage_t(const StageArgs &a, int threads, dim3 grid, cudaStream_t st) {
   size_t smem = stage_smem<R, ANG>(threads, a.nap, a.kc, a.depth, TAU, stage_rows(RC));
-  auto kern = k_stage<R, ANG, RC, ST2, TAU>;
+  auto kern = k_stage<R, ANG, RC, ST2, TAU, AP>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -22,25 +22,25 @@ cudaError_t launch_stage_t(const StageArgs &a, int threads, dim3 grid, cudaStrea
   return cudaGetLastError();
 }
 
-template <typename R, bool ANG, bool TAU>
+template <typename R, bool ANG, bool TAU, bool AP>
 cudaError_t launch_stage_pt(const StageArgs &a, int threads, dim3 grid, cudaStream_t st) {
   if (a.recon == RAD_RECON_PPM)
-    return a.stage2 ? launch_stage_t<R, ANG, RAD_RECON_PPM, true, TAU>(a, threads, grid, st)
-                    : launch_stage_t<R, ANG, RAD_RECON_PPM, false, TAU>(a, threads, grid, st);
+    return a.stage2 ? launch_stage_t<R, ANG, RAD_RECON_PPM, true, TAU, AP>(a, threads, grid, st)
+                    : launch_stage_t<R, ANG, RAD_RECON_PPM, false, TAU, AP>(a, threads, grid, st);
   if (a.recon == RAD_RECON_PLM)
-    return a.stage2 ? launch_stage_t<R, ANG, RAD_RECON_PLM, true, TAU>(a, threads, grid, st)
-                    : launch_stage_t<R, ANG, RAD_RECON_PLM, false, TAU>(a, threads, grid, st);
-  return a.stage2 ? launch_stage_t<R, ANG, RAD_RECON_DC, true, TAU>(a, threads, grid, st)
-                  : launch_stage_t<R, ANG, RAD_RECON_DC, false, TAU>(a, threads, grid, st);
+    return a.stage2 ? launch_stage_t<R, ANG, RAD_RECON_PLM, true, TAU, AP>(a, threads, grid, st)
+                    : launch_stage_t<R, ANG, RAD_RECON_PLM, false, TAU, AP>(a, threads, grid, st);
+  return a.stage2 ? launch_stage_t<R, ANG, RAD_RECON_DC, true, TAU, AP>(a, threads, grid, st)
+                  : launch_stage_t<R, ANG, RAD_RECON_DC, false, TAU, AP>(a, threads, grid, st);
 }
 
-template <typename R, bool ANG>
+template <typename R, bool ANG, bool AP>
 cudaError_t launch_stage_rp(const StageArgs &a, cudaStream_t st) {
   const int threads = (a.nap / 2 + 31) / 32 * 32;     // two bins per consumer thread
   const int nchunk = (a.n3 + a.kc - 1) / a.kc;
   const dim3 grid((unsigned)((long long)a.n1 * a.n2 * nchunk));
-  return a.tau_const > 0.0 ? launch_stage_pt<R, ANG, true>(a, threads, grid, st)
-                           : launch_stage_pt<R, ANG, false>(a, threads, grid, st);
+  return a.tau_const > 0.0 ? launch_stage_pt<R, ANG, true, AP>(a, threads, grid, st)
+                           : launch_stage_pt<R, ANG, false, AP>(a, threads, grid, st);
 }
 
 }  // namespace rad

@@ -51,6 +51,8 @@ __global__ void k_cfl(const ColGeo *cols, int n1, int n2, int ndim, const double
 }  // namespace
 
 cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st) {
+  if (ang && a.recon_ang == RAD_RECON_PLM)
+    return f32 ? launch_stage_rp<float, true, true>(a, st) : launch_stage_rp<double, true, true>(a, st);
   if (f32) return ang ? launch_stage_rp<float, true>(a, st) : launch_stage_rp<float, false>(a, st);
   return ang ? launch_stage_rp<double, true>(a, st) : launch_stage_rp<double, false>(a, st);
 }
@@ -113,6 +115,8 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
   a.slot_nbr = ctx->dang.slot_nbr;
   a.slot_edge = ctx->dang.slot_edge;
   a.edge_pq = ctx->dang.edge_pq;
+  a.edge_line = ctx->dang.edge_line;
+  a.recon_ang = o->recon_ang;
   a.recon = o->recon;
   a.mode = o->coupling;
   a.zero_guard = o->zero_guard;

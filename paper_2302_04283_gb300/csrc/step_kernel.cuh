@@ -71,6 +71,8 @@ struct StageArgs {
   const void *f1, *f2, *f3;
   const double *dir, *dOmega, *edge_geo;
   const int *perm, *slot_nbr, *slot_edge, *edge_pq;
+  const int *edge_line;    // latitude-longitude grids: cell behind p, cell beyond q of each side
+  int recon_ang;           // RAD_RECON_DC or RAD_RECON_PLM (angular fluxes)
   int recon, mode, zero_guard;
   double n0crit, a_rad, gamma;
   double inv_gm1;          // 1 / (gamma - 1)
@@ -82,7 +84,7 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
 cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st);
 // One precision / geometry class of stage launches (explicitly instantiated in
 // stage_<precision>_<flat|ang>.cu, one translation unit each).
-template <typename R, bool ANG>
+template <typename R, bool ANG, bool AP = false>
 cudaError_t launch_stage_rp(const StageArgs &a, cudaStream_t st);
 // RAD_OK, or RAD_EUNSUPPORTED with a message when a stage launch of this
 // grid / bin count cannot be formed (element count, shared memory, threads).
@@ -433,7 +435,8 @@ __host__ __device__ constexpr size_t stage_smem(int threads, int nap, int kc, in
          + (size_t)2 * kMaxStages * 8 + 16;                     // full and empty mbarriers
 }
 
-template <typename R, bool ANG, int RC, bool ST2, bool TAU>
+template <typename R, bool ANG, int RC, bool ST2, bool TAU, bool AP = false>
+// AP: PLM angular reconstruction along the lines of a latitude-longitude grid.
 // Register budget: the flat FP32 DC / PLM kernels are held to 96 registers
 // (the bound of a 544-thread block) so that five 128-thread CTAs fit an SM;
 // the others get 128 (the curved kernels' CTAs are limited by shared memory
@@ -644,7 +647,18 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
         R Pv = len * sp * n0e;
         R PL = sp >= R(0) ? Pv : R(0), PR = sp >= R(0) ? R(0) : Pv;
         R dOn = e ? dO_[1] : dO_[0];
-        if (a.edge_pq[2 * ed] == n) {
+        const bool isp = a.edge_pq[2 * ed] == n;
+        if (AP) {
+          // the flux out of n through this side is cs times the upwind cell's
+          // reconstruction at the side; kept: cs, and packed the neighbour m,
+          // the cell of the upwind line beyond the side (behind n when n is
+          // upwind, beyond m otherwise) and whether n is upwind
+          const bool upn = isp ? sp >= R(0) : sp < R(0);
+          const int *el = a.edge_line + 2 * ed;
+          const int l = upn ? el[isp ? 0 : 1] : el[isp ? 1 : 0];
+          a_nb[e][s] = (isp ? Pv : -Pv) / dOn;
+          nb_m[e][s] = m | (l << 12) | (upn ? 1 << 24 : 0);
+        } else if (isp) {
           self += PL;
           a_nb[e][s] = PR / dOn;
         } else {
@@ -860,9 +874,22 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       R da[2];
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
-        R acc = a_self[e] * (e ? zc.y : zc.x);
+        const R In = e ? zc.y : zc.x;
+        R acc = a_self[e] * In;
 #pragma unroll
-        for (int s2 = 0; s2 < kMaxSlots; ++s2) acc += a_nb[e][s2] * row[nb_m[e][s2]];
+        for (int s2 = 0; s2 < kMaxSlots; ++s2) {
+          if (AP) {
+            // PLM along the grid line: y + q(x, y, z) is the reconstruction of
+            // the upwind cell y at the side towards z, x the cell behind y
+            const int pk = nb_m[e][s2];
+            const R Im = row[pk & 0xfff], Il = row[(pk >> 12) & 0xfff];
+            const bool upn = (pk >> 24) & 1;
+            const R y = upn ? In : Im, z = upn ? Im : In;
+            acc += a_nb[e][s2] * (y + vl_half(Il, y, z));
+          } else {
+            acc += a_nb[e][s2] * row[nb_m[e][s2]];
+          }
+        }
         da[e] = acc;
       }
       divA = P::mk(da[0], da[1]);

@@ -76,7 +76,8 @@ def oracle_gas(w):
     return g
 
 
-def run_both(w, nsteps, precision="f64", recon="plm", coupling=None, dt=None, tau=0.0, rad_dom=False):
+def run_both(w, nsteps, precision="f64", recon="plm", coupling=None, dt=None, tau=0.0, rad_dom=False,
+             recon_ang="dc"):
     """Advance workload w nsteps on the GPU and in the oracle; return both states."""
     st = oracle_setup(w)
     gc = GpuCase(w)
@@ -86,7 +87,7 @@ def run_both(w, nsteps, precision="f64", recon="plm", coupling=None, dt=None, ta
         dt = OCFL.cfl_dt(st, w["cfl"])
     # oracle
     opts = OS.Opts(recon=recon, mode=mode if mode != "none" else "thermal", couple=mode != "none",
-                   tau_const=tau, rad_dom=rad_dom)
+                   tau_const=tau, rad_dom=rad_dom, recon_ang=recon_ang)
     I, T = torch.tensor(w["I0"]), torch.tensor(w["T"])
     gas_o = oracle_gas(w)
     src_tot = torch.zeros(T.shape + (4,), dtype=torch.float64)
@@ -103,7 +104,8 @@ def run_both(w, nsteps, precision="f64", recon="plm", coupling=None, dt=None, ta
              "none": rad.RAD_COUPLE_NONE}[mode]
     o = rad.rad_opts_default(precision=rad.RAD_F64 if precision == "f64" else rad.RAD_F32,
                              recon={"dc": rad.RAD_RECON_DC, "plm": rad.RAD_RECON_PLM, "ppm": rad.RAD_RECON_PPM}[recon],
-                             coupling=cmode, tau_const=tau, rad_dom=int(rad_dom))
+                             coupling=cmode, tau_const=tau, rad_dom=int(rad_dom),
+                             recon_ang=rad.RAD_RECON_PLM if recon_ang == "plm" else rad.RAD_RECON_DC)
     for _ in range(nsteps):
         rad.rad_step(gc.ctx, Ig, gas_g, dt, o, src_g)
     rad.rad_check(gc.ctx)

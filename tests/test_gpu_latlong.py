@@ -63,6 +63,57 @@ def test_step_on_latlong_grid_matches_oracle(name, n, ll, prec, recon, steps):
         r["gc"].close()
 
 
+ANGPLM_CASES = [
+    # name, sizes, (n_zeta, n_psi), precision, spatial recon, steps
+    ("torus3d", (6, 6, 4), (4, 8), "f64", "plm", 2),         # Kerr-Schild 3D: polar, outflow
+    ("torus3d", (6, 6, 4), (6, 12), "f32", "plm", 2),
+    ("torus3d_big", (6, 4, 4), (3, 6), "f64", "dc", 1),      # moving gas, scattering
+    ("torus3d_big", (5, 4, 4), (5, 10), "f32", "ppm", 1),
+    ("adjoint2d", (10, 8, 1), (2, 4), "f64", "plm", 2),      # 2D; two bands: both lines cross a pole
+]
+
+
+@pytest.mark.parametrize("name,n,ll,prec,recon,steps", ANGPLM_CASES)
+def test_angular_plm_on_latlong_grid_matches_oracle(name, n, ll, prec, recon, steps):
+    """PLM along the lat/long grid lines (continued across the poles) for the
+    angular fluxes, against the oracle."""
+    w = W.make(name, n=n, level=1, latlong=ll)
+    r = run_both(w, steps, prec, recon=recon, recon_ang="plm")
+    try:
+        tol = 1e-12 if prec == "f64" else 2e-5
+        assert rel_err(r["I_g"], r["I_o"]) < tol
+        assert rel_err(r["T_g"], r["T_o"]) < tol
+    finally:
+        r["gc"].close()
+
+
+def test_angular_plm_needs_a_latlong_grid():
+    w = W.make("torus3d", n=(4, 4, 2), level=2)
+    gc = GpuCase(w)
+    try:
+        I = torch.zeros((2, 4, 4, gc.n_ap), dtype=torch.float64, device="cuda")
+        with pytest.raises(rad.RadError) as e:
+            rad.rad_step(gc.ctx, I, gc.gas(w), 0.01, rad.rad_opts_default(recon_ang=rad.RAD_RECON_PLM))
+        assert e.value.status == rad.RAD_EUNSUPPORTED
+        with pytest.raises(rad.RadError) as e:
+            rad.rad_step(gc.ctx, I, gc.gas(w), 0.01, rad.rad_opts_default(recon_ang=5))
+        assert e.value.status == rad.RAD_EINVAL
+    finally:
+        gc.close()
+    w = W.make("torus3d", n=(4, 4, 2), level=1, latlong=(2, 4))
+    gc = GpuCase(w)
+    try:
+        I = torch.zeros((2, 4, 4, gc.n_ap), dtype=torch.float64, device="cuda")
+        z = torch.zeros((2, 4, 4), dtype=torch.float64, device="cuda")
+        with pytest.raises(rad.RadError) as e:        # the adjoint covers donor-cell angular fluxes
+            rad.rad_step_adjoint(gc.ctx, I, gc.gas(w), 0.01,
+                                 rad.rad_opts_default(coupling=rad.RAD_COUPLE_NONE, recon_ang=rad.RAD_RECON_PLM),
+                                 I, torch.zeros_like(I), None, None, z, z.clone())
+        assert e.value.status == rad.RAD_EUNSUPPORTED
+    finally:
+        gc.close()
+
+
 def test_cfl_on_latlong_grid_matches_oracle():
     w = W.make("torus3d", n=(6, 6, 4), level=1, latlong=(6, 12), with_intensity=False)
     gc = GpuCase(w)
