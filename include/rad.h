@@ -299,6 +299,14 @@ int rad_loss_outer(rad_ctx *ctx, const void *I, int precision, double *L_dev, vo
  * RAD_OK or the first recorded rad_status. */
 int rad_check(rad_ctx *ctx);
 
+/* Self-test of the bounded device waits (no paper counterpart): enqueue a
+ * kernel that waits on an mbarrier nothing arrives at; after `seconds`
+ * (0 < seconds <= 10) the wait gives up and records the timeout bit that the
+ * stage and moment kernels record, so that the next rad_check returns
+ * RAD_ECUDA ("a device wait timed out").  The context stays usable.
+ * Asynchronous; RAD_EINVAL for a bad duration. */
+int rad_selftest_wait(rad_ctx *ctx, double seconds);
+
 #ifdef __cplusplus
 }
 #endif

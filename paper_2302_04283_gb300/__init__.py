@@ -98,6 +98,7 @@ def lib():
         "rad_step_host": ([_vp, ctypes.c_int, P(rad_host_item), ctypes.c_double, P(rad_opts), ctypes.c_int,
                            ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "rad_check": ([_vp], ctypes.c_int),
+        "rad_selftest_wait": ([_vp, ctypes.c_double], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -244,6 +245,10 @@ def rad_loss_outer(ctx, I, precision, L_dev, dL_dI=None):
 
 def rad_check(ctx):
     _check(ctx, lib().rad_check(ctx))
+
+
+def rad_selftest_wait(ctx, seconds):
+    _check(ctx, lib().rad_selftest_wait(ctx, float(seconds)))
 
 
 def rad_last_error(ctx):

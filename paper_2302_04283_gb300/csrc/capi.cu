@@ -367,6 +367,14 @@ int rad_loss_outer(rad_ctx *ctx, const void *I, int precision, double *L_dev, vo
   return st == RAD_OK ? st : fail(ctx, st, err);
 }
 
+int rad_selftest_wait(rad_ctx *ctx, double seconds) {
+  if (!ctx) return RAD_EINVAL;
+  if (!(seconds > 0.0 && seconds <= 10.0)) return fail(ctx, RAD_EINVAL, "seconds must be in (0, 10]");
+  const cudaError_t ce = rad::launch_wait_selftest(ctx, seconds);
+  if (ce != cudaSuccess) return fail(ctx, RAD_ECUDA, std::string("self-test launch failed: ") + cudaGetErrorString(ce));
+  return RAD_OK;
+}
+
 int rad_check(rad_ctx *ctx) {
   if (!ctx) return RAD_EINVAL;
   int h = 0;
@@ -374,7 +382,7 @@ int rad_check(rad_ctx *ctx) {
   if (ce == cudaSuccess) ce = cudaMemsetAsync(ctx->err_word, 0, sizeof(int), ctx->stream);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
   if (ce != cudaSuccess) return fail(ctx, RAD_ECUDA, std::string("rad_check: ") + cudaGetErrorString(ce));
-  if (h & (1 << 3)) return fail(ctx, RAD_ECUDA, "a device wait timed out (tensor-core moments)");
+  if (h & (1 << 3)) return fail(ctx, RAD_ECUDA, "a device wait timed out (stage pipeline or tensor-core moments)");
   if (h & rad::kErrNoConv) return fail(ctx, RAD_ENOCONV, "a cell's quartic had no bracketed root or did not converge");
   if (h & rad::kErrNonFinite) return fail(ctx, RAD_ENONFINITE, "a non-finite intensity was produced");
   return RAD_OK;

@@ -61,6 +61,7 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  unsigned long long t0 = 0;
   for (long long it = 0; it < kTcSpinLimit; ++it) {
     uint32_t done;
     asm volatile(
@@ -70,6 +71,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((it & 255) == 0) {                       // bounded in time as well as in polls
+      unsigned long long now;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+      if (it == 0) t0 = now;
+      else if (now - t0 > 2000000000ull) return false;
+    }
   }
   return false;
 }

@@ -141,6 +141,7 @@ struct StageArgs;
 int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opts *opts,
                 double *gas_src, void *scratch_I, double *scratch_T, std::string &err);
 int launch_cfl(rad_ctx *ctx, double cfl, double *dt_out, std::string &err);
+cudaError_t launch_wait_selftest(rad_ctx *ctx, double seconds);
 
 // moments.cu
 int launch_moments(rad_ctx *ctx, const void *I, int precision, int frame, int method,

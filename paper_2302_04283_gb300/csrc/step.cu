@@ -48,7 +48,25 @@ __global__ void k_cfl(const ColGeo *cols, int n1, int n2, int ndim, const double
   if (best < INFINITY) atomicMin(out, (unsigned long long)__double_as_longlong(best));
 }
 
+// Self-test of the bounded waits: one warp waits on an mbarrier that nothing
+// ever arrives at; the wait gives up after limit_ns and the error bit of a
+// timed-out wait is set, exactly as in the stage and moment kernels.
+__global__ void k_wait_selftest(int *err, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (threadIdx.x == 0 && !mbar_wait_parity(&bar, 0, limit_ns)) atomicOr(err, 1 << 3);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(rad_ctx *ctx, double seconds) {
+  k_wait_selftest<<<1, 32, 0, ctx->stream>>>(ctx->err_word, (unsigned long long)(seconds * 1e9));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st) {
   if (ang && a.recon_ang == RAD_RECON_PLM)

@@ -393,6 +393,7 @@ constexpr int kStageMaxThreads = 512;   // consumers (two bins each) + one produ
 // row at k + h and the own row of I^0, with h = 2 (DC, PLM) or 3 (PPM)
 __host__ __device__ constexpr int stage_rows(int recon) { return recon == RAD_RECON_PPM ? 15 : 11; }
 constexpr long long kSpinLimit = 1ll << 28;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // a healthy wait takes microseconds
 
 __device__ __forceinline__ uint32_t s_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -408,8 +409,19 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       "l"(src), "r"(bytes), "r"(s_addr(bar))
       : "memory");
 }
-__device__ __forceinline__ bool mbar_wait_parity(uint64_t *bar, uint32_t parity) {
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the given phase parity of an mbarrier; false after limit_ns (or
+// kSpinLimit polls), so that a wait that can no longer complete ends in an
+// error status instead of a stalled kernel.
+__device__ __forceinline__ bool mbar_wait_parity(uint64_t *bar, uint32_t parity,
+                                                 unsigned long long limit_ns = kWaitLimitNs) {
   const uint32_t a = s_addr(bar);
+  unsigned long long t0 = 0;
   for (long long it = 0; it < kSpinLimit; ++it) {
     uint32_t done;
     asm volatile(
@@ -418,6 +430,11 @@ __device__ __forceinline__ bool mbar_wait_parity(uint64_t *bar, uint32_t parity)
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((it & 255) == 0) {
+      const unsigned long long now = global_ns();
+      if (it == 0) t0 = now;
+      else if (now - t0 > limit_ns) return false;
+    }
   }
   return false;
 }

@@ -269,3 +269,28 @@ def test_host_pipeline_matches_device_path(prec):
             assert torch.equal(item["R"], Re)
     finally:
         gc.close()
+
+
+def test_bounded_device_wait_reports_a_timeout():
+    """A device wait on an mbarrier that nothing arrives at gives up after its
+    time limit and records the timeout status, which rad_check reads; the
+    context stays usable (a step afterwards succeeds)."""
+    import time
+    w = W.make("turb3d", n=(4, 4, 4), level=1)
+    gc = GpuCase(w)
+    try:
+        t0 = time.time()
+        rad.rad_selftest_wait(gc.ctx, 0.2)
+        with pytest.raises(rad.RadError) as e:
+            rad.rad_check(gc.ctx)
+        assert e.value.status == rad.RAD_ECUDA and "timed out" in str(e.value)
+        assert 0.15 < time.time() - t0 < 5.0
+        rad.rad_check(gc.ctx)                      # the word was cleared
+        I = gc.to_gpu_I(w["I0"], np.arange(gc.n_ang), torch.float64)
+        rad.rad_step(gc.ctx, I, gc.gas(w), 1e-3, rad.rad_opts_default())
+        rad.rad_check(gc.ctx)
+        with pytest.raises(rad.RadError) as e:
+            rad.rad_selftest_wait(gc.ctx, 0.0)
+        assert e.value.status == rad.RAD_EINVAL
+    finally:
+        gc.close()
