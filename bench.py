@@ -174,7 +174,7 @@ def kernel_fingerprint():
     kernel and its launcher: a profile's counters describe this kernel only
     while the fingerprint it records matches."""
     h = hashlib.sha256()
-    for f in ("step_kernel.cuh", "step.cu"):
+    for f in ("step_kernel.cuh", "stage_launch.cuh", "step.cu"):
         with open(os.path.join(ROOT, "paper_2302_04283_gb300", "csrc", f)) as fh:
             for line in fh:
                 code = line.split("//")[0].strip()

@@ -13,9 +13,11 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
 
-SOURCES = ["angles.cpp", "capi.cu", "geom.cu", "step.cu", "stage_f32_flat.cu", "stage_f32_ang.cu",
-           "stage_f64_flat.cu", "stage_f64_ang.cu", "stage_f32_angplm.cu", "stage_f64_angplm.cu", "moments.cu", "moments_tc.cu", "adjoint.cu", "noalloc.cu",
-           "host_stream.cu", "raddom.cu"]
+SOURCES = ["angles.cpp", "capi.cu", "geom.cu", "step.cu",
+           "stage_f32_flat.cu", "stage_f32_flat164.cu", "stage_f32_ang.cu", "stage_f32_ang164.cu",
+           "stage_f32_ang364.cu", "stage_f32_ang644.cu", "stage_f32_angplm.cu",
+           "stage_f64_flat.cu", "stage_f64_ang.cu", "stage_f64_angplm.cu",
+           "moments.cu", "moments_tc.cu", "adjoint.cu", "noalloc.cu", "host_stream.cu", "raddom.cu"]
 
 
 def _compile(src, extra):
@@ -29,7 +31,7 @@ def _compile(src, extra):
 
 def build(verbose=False, extra=()):
     os.makedirs(BUILD, exist_ok=True)
-    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 2)) as ex:
         results = list(ex.map(lambda s: _compile(s, list(extra)), SOURCES))
     objs = []
     for src, obj, r in results:

@@ -1,0 +1,9 @@
+// FP32 stage kernels with angular fluxes (curved space), specialised for the
+// padded row of the level-4 geodesic grid (162 bins, 164 padded).
+#include "stage_launch.cuh"
+
+namespace rad {
+
+template cudaError_t launch_stage_rp<float, true, false, kNapGeo4>(const StageArgs &a, cudaStream_t st);
+
+}  // namespace rad

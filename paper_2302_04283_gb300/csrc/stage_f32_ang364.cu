@@ -1,0 +1,9 @@
+// FP32 stage kernels with angular fluxes (curved space), specialised for the
+// padded row of the level-6 geodesic grid (362 bins, 364 padded).
+#include "stage_launch.cuh"
+
+namespace rad {
+
+template cudaError_t launch_stage_rp<float, true, false, kNapGeo6>(const StageArgs &a, cudaStream_t st);
+
+}  // namespace rad

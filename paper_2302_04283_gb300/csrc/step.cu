@@ -71,6 +71,12 @@ cudaError_t launch_wait_selftest(rad_ctx *ctx, double seconds) {
 cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st) {
   if (ang && a.recon_ang == RAD_RECON_PLM)
     return f32 ? launch_stage_rp<float, true, true>(a, st) : launch_stage_rp<double, true, true>(a, st);
+  if (f32 && !ang && a.nap == kNapGeo4) return launch_stage_rp<float, false, false, kNapGeo4>(a, st);
+  if (f32 && ang) {
+    if (a.nap == kNapGeo4) return launch_stage_rp<float, true, false, kNapGeo4>(a, st);
+    if (a.nap == kNapGeo6) return launch_stage_rp<float, true, false, kNapGeo6>(a, st);
+    if (a.nap == kNapGeo8) return launch_stage_rp<float, true, false, kNapGeo8>(a, st);
+  }
   if (f32) return ang ? launch_stage_rp<float, true>(a, st) : launch_stage_rp<float, false>(a, st);
   return ang ? launch_stage_rp<double, true>(a, st) : launch_stage_rp<double, false>(a, st);
 }

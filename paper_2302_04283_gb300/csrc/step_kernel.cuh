@@ -84,8 +84,15 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
 cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st);
 // One precision / geometry class of stage launches (explicitly instantiated in
 // stage_<precision>_<flat|ang>.cu, one translation unit each).
-template <typename R, bool ANG, bool AP = false>
+// NAP > 0 fixes the padded row length (a.nap) at compile time; 0 reads it
+// from the arguments.
+template <typename R, bool ANG, bool AP = false, int NAP = 0>
 cudaError_t launch_stage_rp(const StageArgs &a, cudaStream_t st);
+// Padded rows of the level-4, 6 and 8 geodesic grids (162, 362, 642 bins):
+// the FP32 kernels have variants with these row lengths fixed (the flat-space
+// kernel at level 4, the curved-space one at all three), where the constant
+// row stride folds the ring and chunk addressing into immediates.
+constexpr int kNapGeo4 = 164, kNapGeo6 = 364, kNapGeo8 = 644;
 // RAD_OK, or RAD_EUNSUPPORTED with a message when a stage launch of this
 // grid / bin count cannot be formed (element count, shared memory, threads).
 int check_stage(const StageArgs &a, bool f32, std::string &err);
@@ -452,8 +459,9 @@ __host__ __device__ constexpr size_t stage_smem(int threads, int nap, int kc, in
          + (size_t)2 * kMaxStages * 8 + 16;                     // full and empty mbarriers
 }
 
-template <typename R, bool ANG, int RC, bool ST2, bool TAU, bool AP = false>
+template <typename R, bool ANG, int RC, bool ST2, bool TAU, bool AP = false, int NAP = 0>
 // AP: PLM angular reconstruction along the lines of a latitude-longitude grid.
+// NAP: the padded row length when fixed at compile time (0: a.nap).
 // Register budget: the flat FP32 DC / PLM kernels are held to 96 registers
 // (the bound of a 544-thread block) so that five 128-thread CTAs fit an SM;
 // the others get 128 (the curved kernels' CTAs are limited by shared memory
@@ -464,13 +472,14 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   using P = P2<R>;
   using V = typename P::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nap = NAP > 0 ? NAP : a.nap;                  // padded bins per row
   const int t = threadIdx.x;
   const int ncons = blockDim.x - 32;                      // consumer threads; the last warp produces
   const bool cons = t < ncons;
   const int nwarp = ncons >> 5;                           // consumer warps
   const int lane = t & 31, warp = t >> 5;
   const int b0 = 2 * t;                                   // bins b0, b0 + 1
-  const bool inpair = b0 < a.nap;                         // pair inside the padded row
+  const bool inpair = b0 < nap;                         // pair inside the padded row
   const bool act0 = b0 < a.nang, act1 = b0 + 1 < a.nang;
   const int nchunk = (a.n3 + a.kc - 1) / a.kc;
   const int col = blockIdx.x / nchunk;
@@ -479,7 +488,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   const int k0 = chunk * a.kc;
   const int nc = min(a.kc, a.n3 - k0);
   const unsigned ncol = (unsigned)a.n1 * a.n2;
-  const unsigned strideK = ncol * (unsigned)a.nap;        // element offsets fit in 32 bits (host-checked)
+  const unsigned strideK = ncol * (unsigned)nap;        // element offsets fit in 32 bits (host-checked)
   const R *Ip = (const R *)a.Iprev;
   const R *I0 = (const R *)a.I0;
   R *Io = (R *)a.Iout;
@@ -492,8 +501,8 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
 
   // shared memory: staged rows, I* of the chunk, then small per-cell arrays
   R *stg = (R *)smem_raw;                                  // [depth][ROWS][nap]
-  R *sI = stg + a.depth * ROWS * a.nap;                    // [kc][nap]
-  R *sgas = sI + a.kc * a.nap;                             // [kc][5]
+  R *sI = stg + a.depth * ROWS * nap;                    // [kc][nap]
+  R *sgas = sI + a.kc * nap;                             // [kc][5]
   R *red = sgas + a.kc * 5;                                // [kc][nwarp][kNRedC]
   R *sums = red + a.kc * nwarp * kNRedC;                   // [kc][kNRedC]
   R *Sc = sums + a.kc * kNRedC;                            // [kc]
@@ -707,37 +716,37 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
     anypol |= pol != 0;
   }
   const bool d3 = a.ndim >= 3;
-  const size_t rowb = (size_t)a.nap * sizeof(R);
+  const size_t rowb = (size_t)nap * sizeof(R);
   auto kidx = [&](int k) {
     int pol;
     return wrap_idx(k, a.n3, a.bc_lo[2], a.bc_hi[2], pol);
   };
   auto rowp = [&](const R *base, int ii, int jj, int kk) {
-    return base + ((size_t)kk * ncol + (size_t)jj * a.n1 + ii) * a.nap;
+    return base + ((size_t)kk * ncol + (size_t)jj * a.n1 + ii) * nap;
   };
   auto produce = [&](int c, int st) {   // issue the copies of cell k0 + c into ring stage st
     const int k = k0 + c;
-    R *dst = stg + (size_t)st * ROWS * a.nap;
+    R *dst = stg + (size_t)st * ROWS * nap;
     uint32_t bytes = (uint32_t)(X1N * rowb) + (a.ndim >= 2 ? (uint32_t)(X2N * rowb) : 0u) +
                      (d3 ? (uint32_t)rowb : 0u) + (ST2 ? (uint32_t)rowb : 0u);
     mbar_expect_tx(&bars[st], bytes);
     if (x1contig) {
       bulk_g2s(dst, rowp(Ip, i - H, j, k), (uint32_t)(X1N * rowb), &bars[st]);
     } else {
-      for (int q = 0; q < X1N; ++q) bulk_g2s(dst + q * a.nap, rowp(Ip, xs[q], j, k), (uint32_t)rowb, &bars[st]);
+      for (int q = 0; q < X1N; ++q) bulk_g2s(dst + q * nap, rowp(Ip, xs[q], j, k), (uint32_t)rowb, &bars[st]);
     }
     if (a.ndim >= 2) {
       for (int q = 0; q < X2N; ++q) {
         int kk = k;
         if (ypol[q] && a.n3 > 1) kk = (k + a.n3 / 2) % a.n3;
-        bulk_g2s(dst + (SX2 + q) * a.nap, rowp(Ip, i, yj[q], kk), (uint32_t)rowb, &bars[st]);
+        bulk_g2s(dst + (SX2 + q) * nap, rowp(Ip, i, yj[q], kk), (uint32_t)rowb, &bars[st]);
       }
     }
-    if (d3) bulk_g2s(dst + SX3 * a.nap, rowp(Ip, i, j, kidx(k + H)), (uint32_t)rowb, &bars[st]);
-    if (ST2) bulk_g2s(dst + SI0 * a.nap, rowp(I0, i, j, k), (uint32_t)rowb, &bars[st]);
+    if (d3) bulk_g2s(dst + SX3 * nap, rowp(Ip, i, j, kidx(k + H)), (uint32_t)rowb, &bars[st]);
+    if (ST2) bulk_g2s(dst + SI0 * nap, rowp(I0, i, j, k), (uint32_t)rowb, &bars[st]);
   };
   const int p0 = act0 ? a.perm[b0] : 0, p1 = act1 ? a.perm[b0 + 1] : 0;
-  const unsigned own = (unsigned)col * a.nap + (inpair ? b0 : 0);
+  const unsigned own = (unsigned)col * nap + (inpair ? b0 : 0);
   const int bb = inpair ? b0 : 0;
   auto sv = [&](const R *row) -> V { return *(const V *)(row + bb); };
   const R dtR = (R)a.dt, dts = (R)a.dts;
@@ -794,7 +803,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   int st = 0;
   uint32_t ph = 0;                          // parity of the full barrier's current phase
   for (int c = 0; c < (cons ? nc : 0); ++c) {
-    const R *sr = stg + (size_t)st * ROWS * a.nap;
+    const R *sr = stg + (size_t)st * ROWS * nap;
     if (!mbar_wait_parity(&bars[st], ph)) timeout = true;
     V zc, sx = zero;
     // optical-depth factors d of the six faces (zero without the weighting)
@@ -819,7 +828,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       V win[7];
 #pragma unroll
       for (int q = 0; q < 6; ++q) win[q] = pw[q];
-      win[6] = sv(sr + SX3 * a.nap);
+      win[6] = sv(sr + SX3 * nap);
       zc = win[3];
       V loL, loR, hiL, hiR;
       ppm_states<R>(win, loL, loR, hiL, hiR);
@@ -827,7 +836,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
 #pragma unroll
       for (int q = 0; q < 6; ++q) pw[q] = win[q + 1];
     } else if (d3) {
-      const V w4 = sv(sr + SX3 * a.nap);
+      const V w4 = sv(sr + SX3 * nap);
       const V qc = plm ? vl2<R>(w2, w3, w4) : zero;   // slope of k+1
       zc = w2;
       // slopes: qa = slope(k-1), qb = slope(k), qc = slope(k+1)
@@ -839,17 +848,17 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       qa = qb;
       qb = qc;
     } else {
-      zc = sv(sr + H * a.nap);
+      zc = sv(sr + H * nap);
     }
     if (ppm) {
       V v[7];
 #pragma unroll
-      for (int q = 0; q < 7; ++q) v[q] = q == H ? zc : sv(sr + q * a.nap);
+      for (int q = 0; q < 7; ++q) v[q] = q == H ? zc : sv(sr + q * nap);
       V loL, loR, hiL, hiR;
       ppm_states<R>(v, loL, loR, hiL, hiR);
       sx = P::add(sx, divs(0, loL, loR, hiL, hiR, dlo[0], dhi[0]));
     } else {
-      const V m2 = sv(sr), m1 = sv(sr + a.nap), q1 = sv(sr + 3 * a.nap), q2 = sv(sr + 4 * a.nap);
+      const V m2 = sv(sr), m1 = sv(sr + nap), q1 = sv(sr + 3 * nap), q2 = sv(sr + 4 * nap);
       V sm = zero, sc = zero, sp = zero;
       if (plm) {
         sm = vl2<R>(m2, m1, zc);
@@ -863,7 +872,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       v[H] = zc;
 #pragma unroll
       for (int q = 0; q < X2N; ++q) {
-        const R *row = sr + (SX2 + q) * a.nap;
+        const R *row = sr + (SX2 + q) * nap;
         v[q < H ? q : q + 1] = (ANG && anypol && ypol[q]) ? P::mk(row[p0], row[p1]) : sv(row);
       }
       V loL, loR, hiL, hiR;
@@ -873,7 +882,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       V yv[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const R *row = sr + (SX2 + q) * a.nap;
+        const R *row = sr + (SX2 + q) * nap;
         yv[q] = (ANG && anypol && ypol[q]) ? P::mk(row[p0], row[p1]) : sv(row);
       }
       V sm = zero, sc = zero, sp = zero;
@@ -887,7 +896,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
     V divA = zero;
     if (ANG) {
       // the own row of this cell is slot h of the staged x1 block
-      const R *row = sr + H * a.nap;
+      const R *row = sr + H * nap;
       R da[2];
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
@@ -915,11 +924,11 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
     if (ANG) sx = P::add(sx, divA);
     V Us = P::fma(P::mk(-dtR, -dtR), sx, P::mul(fconv, zc));   // L = -(divS + divA)
     if (ST2) {
-      const V U0 = P::mul(fconv, sv(sr + SI0 * a.nap));
+      const V U0 = P::mul(fconv, sv(sr + SI0 * nap));
       Us = P::mul(P::mk(R(0.5), R(0.5)), P::add(U0, Us));
     }
     const V Is = P::mul(Us, inv_f);
-    if (inpair) *(V *)(sI + c * a.nap + b0) = Is;
+    if (inpair) *(V *)(sI + c * nap + b0) = Is;
     if (a.Istar && inpair) *(V *)((R *)a.Istar + (unsigned)(k0 + c) * strideK + own) = Is;
     if (couple) {
       const R *g = sgas + 5 * c;
@@ -1003,7 +1012,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   const bool want_src = couple && a.src;
   for (int c = 0; c < (cons ? nc : 0); ++c) {
     const unsigned kOff = (unsigned)(k0 + c) * strideK;
-    const V Is = inpair ? *(const V *)(sI + c * a.nap + b0) : zero;
+    const V Is = inpair ? *(const V *)(sI + c * nap + b0) : zero;
     V out = Is;
     if (couple) {
       const R *g = sgas + 5 * c;

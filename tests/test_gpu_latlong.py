@@ -46,6 +46,7 @@ LATLONG_CASES = [
     ("torus3d_big", (6, 4, 4), (3, 6), "f64", "dc", 1),      # moving gas, scattering
     ("torus3d_big", (5, 4, 4), (5, 10), "f32", "plm", 1),
     ("adjoint2d", (10, 8, 1), (5, 10), "f64", "plm", 2),     # 2D Kerr-Schild
+    ("turb3d", (5, 4, 6), (9, 18), "f32", "plm", 2),         # 162 bins: the FP32 flat kernel with a fixed row
 ]
 
 

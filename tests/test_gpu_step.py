@@ -96,6 +96,61 @@ def test_largest_level_step_f64():
         r["gc"].close()
 
 
+GEO4_F32_CASES = [
+    # sizes, recon, C (optical depth): the FP32 flat kernels with the row length
+    # of the level-4 geodesic grid (162 bins, 164 padded) fixed at compile time
+    ((6, 5, 12), "dc", 0.0),
+    ((6, 5, 12), "plm", 0.0),
+    ((7, 5, 9), "ppm", 0.0),
+    ((5, 4, 35), "plm", 3.0),          # two x3 chunks, ragged tail
+    ((7, 5, 6), "dc", 3.0),
+    ((7, 5, 6), "ppm", 3.0),
+]
+
+
+@pytest.mark.parametrize("n,recon,C", GEO4_F32_CASES)
+def test_step_f32_level4_specialised_matches_oracle(n, recon, C):
+    """Both stages of the specialised 164-wide FP32 kernels against the oracle
+    (2e-5, as for every FP32 step)."""
+    w = W.make("turb3d", n=n, level=4)
+    r = run_both(w, 2, "f32", recon=recon, tau=C)
+    try:
+        assert r["gc"].n_ang == 162
+        assert rel_err(r["I_g"], r["I_o"]) < TOL32
+        assert rel_err(r["T_g"], r["T_o"]) < TOL32
+        pad = r["I_g_raw"][..., r["gc"].n_ang:]
+        assert pad.abs().max().item() == 0.0
+    finally:
+        r["gc"].close()
+
+
+GEOFIX_ANG_F32_CASES = [
+    # name, sizes, level, recon, C, steps: the FP32 curved-space kernels with
+    # the row length of the level-4, 6 and 8 geodesic grids fixed at compile time
+    ("torus3d", (6, 5, 4), 4, "plm", 0.0, 2),
+    ("torus3d", (6, 5, 4), 4, "dc", 0.0, 1),
+    ("torus3d", (5, 4, 4), 6, "plm", 0.0, 1),
+    ("torus3d", (5, 4, 4), 6, "ppm", 0.0, 1),
+    ("torus3d_big", (3, 4, 6), 8, "plm", 0.0, 1),
+    ("torus3d_big", (4, 4, 4), 4, "plm", 20.0, 1),     # optical-depth weighting, moving gas
+    ("adjoint2d", (10, 8, 1), 4, "plm", 0.0, 2),        # 2D, fixed emissivity
+]
+
+
+@pytest.mark.parametrize("name,n,level,recon,C,steps", GEOFIX_ANG_F32_CASES)
+def test_step_f32_curved_fixed_row_matches_oracle(name, n, level, recon, C, steps):
+    w = W.make(name, n=n, level=level)
+    r = run_both(w, steps, "f32", recon=recon, tau=C)
+    try:
+        assert r["gc"].n_ang == 10 * level ** 2 + 2
+        assert rel_err(r["I_g"], r["I_o"]) < TOL32
+        assert rel_err(r["T_g"], r["T_o"]) < TOL32
+        pad = r["I_g_raw"][..., r["gc"].n_ang:]
+        assert pad.abs().max().item() == 0.0
+    finally:
+        r["gc"].close()
+
+
 TAU_CASES = [
     # name, sizes, level, precision, recon, C
     ("turb3d", (7, 5, 6), 2, "f64", "plm", 3.0),       # flat, periodic, moving gas
