@@ -258,11 +258,15 @@ typedef struct {
 /*
  * For each of n_items items: copy I and the gas state to the device, take
  * nsteps rad_step steps (no gas source), contract with rad_moments (frame,
- * method as there), and copy R, T (and I_out if given) back.  Two device
- * slots owned by the context alternate; the copies run on a second stream
- * and the moment contraction on a third, so that each overlaps the steps of
- * the neighbouring item (the copies hide when the host buffers are pinned).  Synchronous: returns when every result is in
- * host memory.  Errors as rad_step / rad_moments; a null host array of an
+ * method as there), and copy R, T (and I_out if given) back.  Three device
+ * slots owned by the context rotate (item i in slot i mod 3); uploads,
+ * moment contractions and read-backs run on three streams of their own, so
+ * that the uploads of the next two items and the contraction and read-back
+ * of the previous one overlap the steps of item i (the copies hide when the
+ * host buffers are pinned).  Items in flight together are independent: an
+ * output array (T, R, I_out) of one item must not be an array of another
+ * item among the two before or after it (inputs may be shared).
+ * Synchronous: returns when every result is in host memory.  Errors as rad_step / rad_moments; a null host array of an
  * item is RAD_EINVAL and nothing is enqueued.
  */
 int rad_step_host(rad_ctx *ctx, int n_items, const rad_host_item *items, double dt,

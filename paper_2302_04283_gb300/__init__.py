@@ -211,7 +211,7 @@ def rad_step_host(ctx, items, dt, opts, nsteps, frame, method):
     """items: list of dicts of host (CPU, ideally pinned) tensors with keys
     I, rho, u, alpha_a, alpha_s, eta (or None), T (in/out), R (out) and
     optionally I_out.  Copies in, steps, takes the moments and copies back,
-    overlapping the copies of one item with the compute of the other."""
+    overlapping the copies of neighbouring items with each item's steps."""
     arr = (rad_host_item * max(1, len(items)))()
     for n, it in enumerate(items):
         for k in ("I", "rho", "u", "alpha_a", "alpha_s", "T", "R"):

@@ -68,13 +68,16 @@ void rad_destroy(rad_ctx *ctx) {
   cudaFree(ctx->loss_buf);
   if (ctx->copy_stream) {
     cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamSynchronize(ctx->back_stream);
     cudaStreamSynchronize(ctx->mom_stream);
     cudaStreamDestroy(ctx->copy_stream);
+    cudaStreamDestroy(ctx->back_stream);
     cudaStreamDestroy(ctx->mom_stream);
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < rad_ctx::kHostSlots; ++s) {
       cudaEventDestroy(ctx->ev_h2d[s]);
       cudaEventDestroy(ctx->ev_step[s]);
       cudaEventDestroy(ctx->ev_done[s]);
+      cudaEventDestroy(ctx->ev_back[s]);
     }
   }
   cudaFree(ctx->host_slot_buf);

@@ -2,17 +2,16 @@
 //
 // For each item the intensity and the gas state are copied to the device,
 // advanced by rad_step, contracted by rad_moments, and the moments (plus the
-// updated temperature and, on request, the intensity) are copied back.  Two
-// device slots alternate: the copies of one item run on a second stream
-// while the context stream computes the other, so that with pinned host
-// buffers the transfer time hides behind the kernels.  The paper has no
-// counterpart (it assumes the fields are resident).
-//
-// Order on the copy stream: H2D(0), then for every item i: H2D(i + 1) (after
-// the compute of item i - 1 has released that slot), D2H(i) (after the
-// compute of item i).  The context stream waits for H2D(i) and runs the steps
-// of item i; a third stream runs its moment contraction, so that the
-// (bandwidth-bound) contraction of one item overlaps the steps of the next.
+// updated temperature and, on request, the intensity) are copied back.  Three
+// device slots rotate, and four streams share the work: uploads (copy
+// stream), steps (the context stream), moment contractions (moment stream)
+// and read-backs (back stream).  Item i lives in slot i mod 3; its upload
+// waits only until the item that held the slot before it (i - 3) has been
+// contracted and read back, so the uploads of the next two items run while
+// item i steps, and the read-backs use the other direction of the link
+// concurrently.  With pinned host buffers the step rate is then set by the
+// slower of the kernels and the upload.  The paper has no counterpart (it
+// assumes the fields are resident).
 #include <cstring>
 
 #include "rad_internal.h"
@@ -56,27 +55,30 @@ extern "C" int rad_step_host(rad_ctx *ctx, int n_items, const rad_host_item *ite
   const size_t bI = ncell * ctx->ang.n_ap * esz, bC = ncell * sizeof(double), bR = ncell * 10 * esz;
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t per_slot = up(bI) + 6 * up(bC) + up(3 * bC) + up(bR);
-  if (ctx->host_slot_bytes < 2 * per_slot) {
+  constexpr int NS = rad_ctx::kHostSlots;
+  if (ctx->host_slot_bytes < NS * per_slot) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->host_slot_buf);
     ctx->host_slot_buf = nullptr;
     ctx->host_slot_bytes = 0;
-    if (cudaMalloc(&ctx->host_slot_buf, 2 * per_slot) != cudaSuccess)
+    if (cudaMalloc(&ctx->host_slot_buf, NS * per_slot) != cudaSuccess)
       return fail_h(ctx, RAD_ENOMEM, "rad_step_host: slot allocation failed");
-    ctx->host_slot_bytes = 2 * per_slot;
+    ctx->host_slot_bytes = NS * per_slot;
   }
   if (!ctx->copy_stream) {
     if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->back_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->mom_stream, cudaStreamNonBlocking) != cudaSuccess)
       return fail_h(ctx, RAD_ECUDA, "rad_step_host: stream creation failed");
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NS; ++s) {
       cudaEventCreateWithFlags(&ctx->ev_h2d[s], cudaEventDisableTiming);
       cudaEventCreateWithFlags(&ctx->ev_step[s], cudaEventDisableTiming);
       cudaEventCreateWithFlags(&ctx->ev_done[s], cudaEventDisableTiming);
+      cudaEventCreateWithFlags(&ctx->ev_back[s], cudaEventDisableTiming);
     }
   }
-  Slot slot[2];
-  for (int s = 0; s < 2; ++s) {
+  Slot slot[NS];
+  for (int s = 0; s < NS; ++s) {
     unsigned char *p = (unsigned char *)ctx->host_slot_buf + s * per_slot;
     slot[s].I = p;
     p += up(bI);
@@ -89,10 +91,15 @@ extern "C" int rad_step_host(rad_ctx *ctx, int n_items, const rad_host_item *ite
     p += up(3 * bC) + up(bC);                    // u, and one spare field
     slot[s].R = p;
   }
-  cudaStream_t cs = ctx->copy_stream, ks = ctx->stream, ms = ctx->mom_stream;
+  cudaStream_t cs = ctx->copy_stream, bs = ctx->back_stream, ks = ctx->stream, ms = ctx->mom_stream;
   auto h2d = [&](int i) {
     const rad_host_item &it = items[i];
-    Slot &sl = slot[i & 1];
+    const int s = i % NS;
+    Slot &sl = slot[s];
+    if (i >= NS) {   // item i - NS held the slot: its contraction and read-back must be over
+      cudaStreamWaitEvent(cs, ctx->ev_done[s], 0);
+      cudaStreamWaitEvent(cs, ctx->ev_back[s], 0);
+    }
     cudaMemcpyAsync(sl.I, it.I, bI, cudaMemcpyHostToDevice, cs);
     cudaMemcpyAsync(sl.rho, it.rho, bC, cudaMemcpyHostToDevice, cs);
     cudaMemcpyAsync(sl.u, it.u, 3 * bC, cudaMemcpyHostToDevice, cs);
@@ -100,30 +107,31 @@ extern "C" int rad_step_host(rad_ctx *ctx, int n_items, const rad_host_item *ite
     cudaMemcpyAsync(sl.as, it.alpha_s, bC, cudaMemcpyHostToDevice, cs);
     if (with_eta) cudaMemcpyAsync(sl.eta, it.eta, bC, cudaMemcpyHostToDevice, cs);
     cudaMemcpyAsync(sl.T, it.T, bC, cudaMemcpyHostToDevice, cs);
-    cudaEventRecord(ctx->ev_h2d[i & 1], cs);
+    cudaEventRecord(ctx->ev_h2d[s], cs);
   };
   auto d2h = [&](int i) {
     const rad_host_item &it = items[i];
-    Slot &sl = slot[i & 1];
-    cudaStreamWaitEvent(cs, ctx->ev_done[i & 1], 0);
-    cudaMemcpyAsync(it.R, sl.R, bR, cudaMemcpyDeviceToHost, cs);
-    cudaMemcpyAsync(it.T, sl.T, bC, cudaMemcpyDeviceToHost, cs);
-    if (it.I_out) cudaMemcpyAsync(it.I_out, sl.I, bI, cudaMemcpyDeviceToHost, cs);
+    const int s = i % NS;
+    Slot &sl = slot[s];
+    cudaStreamWaitEvent(bs, ctx->ev_done[s], 0);
+    cudaMemcpyAsync(it.R, sl.R, bR, cudaMemcpyDeviceToHost, bs);
+    cudaMemcpyAsync(it.T, sl.T, bC, cudaMemcpyDeviceToHost, bs);
+    if (it.I_out) cudaMemcpyAsync(it.I_out, sl.I, bI, cudaMemcpyDeviceToHost, bs);
+    cudaEventRecord(ctx->ev_back[s], bs);
   };
-  // the copy and moment streams must not start before work already queued on
-  // the context stream (an earlier call may still be using the slots)
-  cudaEventRecord(ctx->ev_done[0], ks);
-  cudaStreamWaitEvent(cs, ctx->ev_done[0], 0);
-  cudaStreamWaitEvent(ms, ctx->ev_done[0], 0);
-  h2d(0);
+  // the other streams must not start before work already queued on the
+  // context stream (it may still be using device data the caller handed in)
+  cudaEventRecord(ctx->ev_step[0], ks);
+  cudaStreamWaitEvent(cs, ctx->ev_step[0], 0);
+  cudaStreamWaitEvent(bs, ctx->ev_step[0], 0);
+  cudaStreamWaitEvent(ms, ctx->ev_step[0], 0);
+  for (int i = 0; i < NS - 1 && i < n_items; ++i) h2d(i);
   int st = RAD_OK;
   for (int i = 0; i < n_items && st == RAD_OK; ++i) {
-    if (i + 1 < n_items) {
-      if (i >= 1) cudaStreamWaitEvent(cs, ctx->ev_done[(i + 1) & 1], 0);   // slot of item i - 1 released
-      h2d(i + 1);
-    }
-    Slot &sl = slot[i & 1];
-    cudaStreamWaitEvent(ks, ctx->ev_h2d[i & 1], 0);
+    if (i + NS - 1 < n_items) h2d(i + NS - 1);
+    const int s = i % NS;
+    Slot &sl = slot[s];
+    cudaStreamWaitEvent(ks, ctx->ev_h2d[s], 0);
     rad_gas g;
     g.rho = sl.rho;
     g.u = sl.u;
@@ -131,23 +139,24 @@ extern "C" int rad_step_host(rad_ctx *ctx, int n_items, const rad_host_item *ite
     g.alpha_s = sl.as;
     g.eta = with_eta ? sl.eta : nullptr;
     g.T = sl.T;
-    for (int s = 0; s < nsteps && st == RAD_OK; ++s) st = rad_step(ctx, sl.I, &g, dt, o, nullptr);
-    cudaEventRecord(ctx->ev_step[i & 1], ks);
-    cudaStreamWaitEvent(ms, ctx->ev_step[i & 1], 0);
+    for (int q = 0; q < nsteps && st == RAD_OK; ++q) st = rad_step(ctx, sl.I, &g, dt, o, nullptr);
+    cudaEventRecord(ctx->ev_step[s], ks);
+    cudaStreamWaitEvent(ms, ctx->ev_step[s], 0);
     if (st == RAD_OK) {
       std::string err;
       st = rad::launch_moments(ctx, sl.I, o->precision, frame, method, &g, sl.R, ms, err);
       if (st != RAD_OK) fail_h(ctx, st, err);
     }
-    cudaEventRecord(ctx->ev_done[i & 1], ms);
+    cudaEventRecord(ctx->ev_done[s], ms);
     d2h(i);
   }
   cudaError_t ce = cudaStreamSynchronize(cs);
+  cudaError_t be = cudaStreamSynchronize(bs);
   cudaError_t me = cudaStreamSynchronize(ms);
   cudaError_t ke = cudaStreamSynchronize(ks);
   if (st != RAD_OK) return st;      // rad_step / the moments set the message
-  if (ce != cudaSuccess || me != cudaSuccess || ke != cudaSuccess) {
-    const cudaError_t e = ce != cudaSuccess ? ce : (me != cudaSuccess ? me : ke);
+  if (ce != cudaSuccess || be != cudaSuccess || me != cudaSuccess || ke != cudaSuccess) {
+    const cudaError_t e = ce != cudaSuccess ? ce : (be != cudaSuccess ? be : (me != cudaSuccess ? me : ke));
     return fail_h(ctx, RAD_ECUDA, std::string("rad_step_host: ") + cudaGetErrorString(e));
   }
   return RAD_OK;

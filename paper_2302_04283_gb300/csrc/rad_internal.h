@@ -123,11 +123,13 @@ struct rad_ctx {
   // per-row partials of the outgoing-flux loss
   double *loss_buf = nullptr;
   int loss_rows = 0;
-  // rad_step_host: two device slots, a copy stream and its events
+  // rad_step_host: kHostSlots device slots, the upload, read-back and moment
+  // streams and the per-slot events
+  static constexpr int kHostSlots = 3;
   void *host_slot_buf = nullptr;
   size_t host_slot_bytes = 0;
-  cudaStream_t copy_stream = nullptr, mom_stream = nullptr;
-  cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_step[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr, back_stream = nullptr, mom_stream = nullptr;
+  cudaEvent_t ev_h2d[kHostSlots] = {}, ev_step[kHostSlots] = {}, ev_done[kHostSlots] = {}, ev_back[kHostSlots] = {};
 };
 
 namespace rad {
