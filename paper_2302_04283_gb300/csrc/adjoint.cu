@@ -14,6 +14,12 @@
 //                      (k_transport_adj: gather form of the transposed
 //                      PLM / DC upwind stencil and of the angular fluxes)
 // with (a, b, beta) = (0, 1, 1) for stage 1 and (1/2, 1/2, 1/2) for stage 2.
+// With the optical-depth weighting of Sec. 2.4 every face's lambda weight
+// carries the face's factor (1 +- d), and the factor's dependence on
+// alpha_E = alpha_a + alpha_s (through f = -expm1(-tau^2)) gives a further
+// opacity gradient: each cell reduces over bins the flux derivative of its
+// lower face in each dimension (k_transport_adj), and k_tau_grad adds the
+// two faces on either side of a cell to dL/dalpha_a and dL/dalpha_s.
 // The PLM limiter is differentiated on its active branch.  Boundary
 // conditions enter through the transpose of the neighbour map: periodic
 // wrap and outflow clamp by matching every stencil position's source cell
@@ -122,6 +128,10 @@ struct AdjArgs {
   double wTa, wTb;
   int accTa;
   const ColGeo *cols64;  // FP64 column geometry (the thermal reverse sweep runs in FP64)
+  // optical-depth weighting: per cell and dimension, the bin sum over the
+  // cell's lower face of dL/df * df/d(face alpha_E) (written by
+  // k_transport_adj, read by k_tau_grad)
+  double *gtau;
 };
 
 // Three-value CTA reduction used per cell: warp reduce-scatter, then every
@@ -349,8 +359,15 @@ __device__ __forceinline__ void dphi(bool plm, bool right, R v0, R v1, R v2, R d
   }
 }
 
+// Van Leer half-slope q(v0, v1, v2) of the middle cell (0 at extrema).
+template <typename R>
+__device__ __forceinline__ R half_slope(R v0, R v1, R v2) {
+  const R dl = v1 - v0, dr = v2 - v1;
+  return dl * dr > R(0) ? dl * dr / (dl + dr) : R(0);
+}
+
 // Transposed transport of one stage (gather form, one thread per target bin).
-template <typename R, bool ANG, int MAXT>
+template <typename R, bool ANG, int MAXT, bool TAU>
 __global__ void __launch_bounds__(MAXT) k_transport_adj(AdjArgs A) {
   using Col = typename GeoTypes<R>::Col;
   using Face = typename GeoTypes<R>::Face;
@@ -483,9 +500,13 @@ __global__ void __launch_bounds__(MAXT) k_transport_adj(AdjArgs A) {
     return 2 * N[d] - 1 - p;
   };
   R *outA = (R *)A.outA, *outB = (R *)A.outB;
+  constexpr bool tauw = TAU;                       // optical-depth weighting (a.tau_const > 0)
+  __shared__ R tbuf[TAU ? (MAXT / 32) * 4 : 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int c = 0; c < nc; ++c) {
     const int k = k0 + c;
     y[2] = k;
+    R gt[3] = {R(0), R(0), R(0)};   // lower-face sums of this bin (optical-depth weighting)
     auto addr = [&](int ii, int jj, int kk, int bin) -> long long {
       return (long long)kk * strideK + ((long long)jj * a.n1 + ii) * a.nap + bin;
     };
@@ -513,6 +534,38 @@ __global__ void __launch_bounds__(MAXT) k_transport_adj(AdjArgs A) {
         if (t >= 1 && t <= 5) m5[t - 1] = (ghost && a.bc_lo[d] != RAD_BC_PERIODIC) || !act ? R(0)
                                                                                          : mu[addr(ii, jj, kk, bin)];
       }
+      // optical-depth weighting: 1 / n^0bar of the cells at positions -2..2
+      // and, per face t (positions t - 2 | t - 1), d_t and df/d(alpha_E)
+      R nbi[5], fdt[4], dfa[4];
+      if (tauw) {
+        R ux5[5], uy5[5], uz5[5], ae5[5];
+        for (int t = 0; t < 5; ++t) {
+          bool ghost, pol;
+          const int q = src_idx(d, y[d] + t - 2, ghost, pol);
+          int ii = i, jj = j, kk = k;
+          if (d == 0) ii = q;
+          if (d == 1) jj = q;
+          if (d == 2) kk = q;
+          if (pol) kk = a.n3 > 1 ? (k + a.n3 / 2) % a.n3 : k;
+          const long long cell = (long long)kk * ncol + (long long)jj * a.n1 + ii;
+          ux5[t] = (R)a.u[3 * cell];
+          uy5[t] = (R)a.u[3 * cell + 1];
+          uz5[t] = (R)a.u[3 * cell + 2];
+          ae5[t] = (R)a.aa[cell] + (R)a.as[cell];
+          const R u0 = sqrt(R(1) + ux5[t] * ux5[t] + uy5[t] * uy5[t] + uz5[t] * uz5[t]);
+          nbi[t] = R(1) / (u0 - (ux5[t] * nh0 + uy5[t] * nh1 + uz5[t] * nh2));
+        }
+        for (int t = 0; t < 4; ++t) {
+          const R fx = R(0.5) * (ux5[t] + ux5[t + 1]), fy = R(0.5) * (uy5[t] + uy5[t + 1]),
+                  fz = R(0.5) * (uz5[t] + uz5[t + 1]);
+          const R u0F = sqrt(R(1) + fx * fx + fy * fy + fz * fz);
+          const R tdt = (R)a.tau_const * (R)a.dt / u0F;           // dtau / d(face alpha_E)
+          const R tq = tdt * (R(0.5) * (ae5[t] + ae5[t + 1]));
+          const R f = -rexpm1(-tq * tq);
+          fdt[t] = R(0.5) * f * (nbi[t] - nbi[t + 1]);
+          dfa[t] = R(2) * tq * (R(1) - f) * tdt;                     // df/dtau dtau/d(face alpha_E)
+        }
+      }
       for (int t = 0; t < 4; ++t) {
         if (d == 2) {   // x3 faces exist unless they lie beyond a non-periodic boundary
           const int cf = k + t - 2;
@@ -520,9 +573,17 @@ __global__ void __launch_bounds__(MAXT) k_transport_adj(AdjArgs A) {
         }
         if (!fex[d][t]) continue;
         // face between positions cr = t - 2 and cr + 1 (window index t + 1, t + 2)
-        const R lphi = -cA[d][t] * ivd[d][t] * m5[t] + cA[d][t] * ivd[d][t + 1] * m5[t + 1];
+        R lphi = -cA[d][t] * ivd[d][t] * m5[t] + cA[d][t] * ivd[d][t + 1] * m5[t + 1];
         const bool right = uR[d][t];
         const int s0 = right ? t + 1 : t;          // window index of the stencil's first cell
+        if (tauw) {
+          if (t == 1) {   // this cell's lower face: the flux's derivative in f
+            const R ph = right ? v[3] - (plm ? half_slope(v[2], v[3], v[4]) : R(0))
+                               : v[2] + (plm ? half_slope(v[1], v[2], v[3]) : R(0));
+            gt[d] = lphi * ph * (right ? R(-0.5) : R(0.5)) * (nbi[1] - nbi[2]) * dfa[1];
+          }
+          lphi *= right ? R(1) - fdt[t] : R(1) + fdt[t];
+        }
         R dd[3];
         dphi(plm, right, v[s0], v[s0 + 1], v[s0 + 2], dd);
         R g = R(0);
@@ -543,8 +604,21 @@ __global__ void __launch_bounds__(MAXT) k_transport_adj(AdjArgs A) {
       const bool needed = lo ? !u : u;              // stencil reaching row -1 (or n2)
       if (needed) {
         const int jl = fi - 1, jr = fi;
-        const R lphi = -cAf * cols[jl * a.n1 + i].invdV * mu[addr(i, jl, kk, bp)] +
-                       cAf * cols[jr * a.n1 + i].invdV * mu[addr(i, jr, kk, bp)];
+        R lphi = -cAf * cols[jl * a.n1 + i].invdV * mu[addr(i, jl, kk, bp)] +
+                 cAf * cols[jr * a.n1 + i].invdV * mu[addr(i, jr, kk, bp)];
+        if (tauw) {   // the factor of this face for bin bp (upwind side: the left cell for lo)
+          const long long cl = (long long)kk * ncol + (long long)jl * a.n1 + i, cr = cl + a.n1;
+          const R uxl = (R)a.u[3 * cl], uyl = (R)a.u[3 * cl + 1], uzl = (R)a.u[3 * cl + 2];
+          const R uxr = (R)a.u[3 * cr], uyr = (R)a.u[3 * cr + 1], uzr = (R)a.u[3 * cr + 2];
+          const R fx = R(0.5) * (uxl + uxr), fy = R(0.5) * (uyl + uyr), fz = R(0.5) * (uzl + uzr);
+          const R tq = (R)a.tau_const * (R(0.5) * ((R)a.aa[cl] + (R)a.as[cl] + (R)a.aa[cr] + (R)a.as[cr])) *
+                       (R)a.dt / sqrt(R(1) + fx * fx + fy * fy + fz * fz);
+          const R f = -rexpm1(-tq * tq);
+          const R nl = R(1) / (sqrt(R(1) + uxl * uxl + uyl * uyl + uzl * uzl) - (uxl * px + uyl * py + uzl * pz));
+          const R nr = R(1) / (sqrt(R(1) + uxr * uxr + uyr * uyr + uzr * uzr) - (uxr * px + uyr * py + uzr * pz));
+          const R df = R(0.5) * f * (nl - nr);
+          lphi *= lo ? R(1) + df : R(1) - df;
+        }
         R dd[3];
         if (lo) {   // stencil (-1, 0, 1) of the left cell 0; position -1 is this cell
           dphi(plm, false, Il[eown], Il[addr(i, 0, kk, bp)], Il[addr(i, 1, kk, bp)], dd);
@@ -560,6 +634,14 @@ __global__ void __launch_bounds__(MAXT) k_transport_adj(AdjArgs A) {
       for (int s = 0; s < kMaxSlots; ++s) ga += at_nb[s] * mu[addr(i, j, k, nb_m[s])];
       lam -= ga;
     }
+    if (tauw) {
+      R gs[3];
+      cta_sum3(gt[0], gt[1], gt[2], tbuf, nwarp, lane, warp, gs);
+      if (threadIdx.x == 0) {
+        const long long cell = (long long)k * ncol + (long long)j * a.n1 + i;
+        for (int d = 0; d < 3; ++d) A.gtau[3 * cell + d] = (double)gs[d];
+      }
+    }
     if (act) {
       R ra = (R)A.wAf * fconv * mu0 + (R)A.wAL * lam;
       outA[eown] = A.accA ? outA[eown] + ra : ra;
@@ -571,6 +653,32 @@ __global__ void __launch_bounds__(MAXT) k_transport_adj(AdjArgs A) {
   }
 }
 
+// dL/dalpha_a and dL/dalpha_s through the optical-depth weighting, one thread
+// per cell: the sums of its lower faces (its own gtau) and of its upper faces
+// (the next cell's gtau along each dimension, wrapping where periodic; a
+// non-periodic upper boundary face carries none: outflow copies the
+// velocity, so d = 0 there, and polar faces have zero area).  The face
+// alpha_E is the mean of its two cells', hence the 1/2; w = the stage's
+// weight of the transport operator (beta dt).
+__global__ void k_tau_grad(const double *gtau, int n1, int n2, int n3, int ndim, int per0, int per1, int per2,
+                           double w, double *g_aa, double *g_as) {
+  const long long ncell = (long long)n1 * n2 * n3;
+  const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (cell >= ncell) return;
+  const int N[3] = {n1, n2, n3}, per[3] = {per0, per1, per2};
+  const int x[3] = {(int)(cell % n1), (int)((cell / n1) % n2), (int)(cell / ((long long)n1 * n2))};
+  const long long stride[3] = {1, n1, (long long)n1 * n2};
+  double g = 0.0;
+  for (int d = 0; d < ndim; ++d) {
+    g += gtau[3 * cell + d];
+    if (x[d] + 1 < N[d]) g += gtau[3 * (cell + stride[d]) + d];
+    else if (per[d]) g += gtau[3 * (cell - (long long)(N[d] - 1) * stride[d]) + d];
+  }
+  const double ge = 0.5 * w * g;
+  g_aa[cell] += ge;
+  g_as[cell] += ge;
+}
+
 namespace {
 
 template <typename R, bool ANG>
@@ -578,10 +686,29 @@ cudaError_t launch_transport_adj(const AdjArgs &A, cudaStream_t st) {
   int threads = (A.s.nap + 31) / 32 * 32;
   int nchunk = (A.s.n3 + A.s.kc - 1) / A.s.kc;
   dim3 grid((unsigned)((long long)A.s.n1 * A.s.n2 * nchunk));
-  if (threads <= 256) k_transport_adj<R, ANG, 256><<<grid, threads, 0, st>>>(A);
-  else if (threads <= 512) k_transport_adj<R, ANG, 512><<<grid, threads, 0, st>>>(A);
-  else k_transport_adj<R, ANG, 1024><<<grid, threads, 0, st>>>(A);
+  const bool tau = A.s.tau_const > 0.0;
+  if (threads <= 256)
+    tau ? k_transport_adj<R, ANG, 256, true><<<grid, threads, 0, st>>>(A)
+        : k_transport_adj<R, ANG, 256, false><<<grid, threads, 0, st>>>(A);
+  else if (threads <= 512)
+    tau ? k_transport_adj<R, ANG, 512, true><<<grid, threads, 0, st>>>(A)
+        : k_transport_adj<R, ANG, 512, false><<<grid, threads, 0, st>>>(A);
+  else
+    tau ? k_transport_adj<R, ANG, 1024, true><<<grid, threads, 0, st>>>(A)
+        : k_transport_adj<R, ANG, 1024, false><<<grid, threads, 0, st>>>(A);
+  if (tau) {
+    const StageArgs &a = A.s;
+    const long long ncell = (long long)a.n1 * a.n2 * a.n3;
+    k_tau_grad<<<(unsigned)((ncell + 255) / 256), 256, 0, st>>>(
+        A.gtau, a.n1, a.n2, a.n3, a.ndim, a.bc_lo[0] == RAD_BC_PERIODIC, a.bc_lo[1] == RAD_BC_PERIODIC,
+        a.bc_lo[2] == RAD_BC_PERIODIC, A.wAL, A.g_aa, A.g_as);
+  }
   return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_transport_adj_any(const AdjArgs &A, bool ang, cudaStream_t st) {
+  return ang ? launch_transport_adj<R, true>(A, st) : launch_transport_adj<R, false>(A, st);
 }
 
 template <typename R>
@@ -607,7 +734,7 @@ int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
   const size_t esz = f32 ? 4 : 8;
   const size_t ib = (ncell * ctx->ang.n_ap * esz + 255) / 256 * 256;
   const size_t tb = (ncell * sizeof(double) + 255) / 256 * 256;
-  const size_t need = 5 * ib + 3 * tb;
+  const size_t need = 5 * ib + 6 * tb;
   if (ctx->adj_bytes < need) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->adj_buf);
@@ -623,6 +750,7 @@ int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
   void *I1 = p, *I1s = p + ib, *I2s = p + 2 * ib, *mu = p + 3 * ib, *lamI1 = p + 4 * ib;
   double *T1 = (double *)(p + 5 * ib), *T2 = (double *)(p + 5 * ib + tb);
   double *lamT1 = (double *)(p + 5 * ib + 2 * tb);   // adjoint of the stage-1 temperature
+  double *gtau = (double *)(p + 5 * ib + 3 * tb);    // [cell][3] lower-face sums (optical-depth weighting)
   const bool thermal = o->coupling == RAD_COUPLE_THERMAL;
   if (!thermal && lamT_n && lamT_n != lamT_np1) {
     // the temperature passes through an uncoupled or fixed-emissivity step
@@ -670,6 +798,7 @@ int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
   A.g_as = g_as;
   A.g_eta = g_eta;
   A.cols64 = G.cols;
+  A.gtau = gtau;
   // temperature adjoint (thermal coupling): stage 2 takes lambda_T of the
   // step's output, T- = (T^0 + T^1) / 2 splits its lambda_T- in halves to
   // T^0 (lamT_n) and T^1 (lamT1); stage 1 takes lamT1 and adds its
@@ -697,8 +826,7 @@ int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
     A.outB = lam_n;
     A.wBf = 0.5;
     A.accB = 0;
-    ce = f32 ? (ang ? launch_transport_adj<float, true>(A, ctx->stream) : launch_transport_adj<float, false>(A, ctx->stream))
-             : (ang ? launch_transport_adj<double, true>(A, ctx->stream) : launch_transport_adj<double, false>(A, ctx->stream));
+    ce = f32 ? launch_transport_adj_any<float>(A, ang, ctx->stream) : launch_transport_adj_any<double>(A, ang, ctx->stream);
   }
   // ---- stage 1 backwards
   if (ce == cudaSuccess) {
@@ -721,8 +849,7 @@ int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
     A.wAL = dt;
     A.accA = 1;
     A.outB = nullptr;
-    ce = f32 ? (ang ? launch_transport_adj<float, true>(A, ctx->stream) : launch_transport_adj<float, false>(A, ctx->stream))
-             : (ang ? launch_transport_adj<double, true>(A, ctx->stream) : launch_transport_adj<double, false>(A, ctx->stream));
+    ce = f32 ? launch_transport_adj_any<float>(A, ang, ctx->stream) : launch_transport_adj_any<double>(A, ang, ctx->stream);
   }
   if (ce != cudaSuccess) {
     err = std::string("adjoint launch failed: ") + cudaGetErrorString(ce);

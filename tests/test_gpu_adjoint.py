@@ -330,3 +330,92 @@ def test_frozen_temperature_passes_its_adjoint_through():
         assert float(lTn.abs().max()) == 0.0
     finally:
         gc.close()
+
+
+def _moving(w, seed=8, vmax=0.3):
+    """Give a gas at rest random velocities (the optical-depth weighting acts
+    only across velocity differences)."""
+    if not np.any(w["u"]):
+        rng = np.random.default_rng(seed)
+        v = rng.uniform(-1, 1, w["u"].shape)
+        v *= vmax / np.sqrt((v * v).sum(-1)).max()
+        w["u"] = v / np.sqrt(1 - (v * v).sum(-1))[..., None]
+    return w
+
+
+TAU_ADJ_CASES = [
+    # name, sizes, level, recon, coupling, C, precision
+    ("turb3d", (6, 5, 7), 2, "plm", "emissivity", 3.0, "f64"),      # flat, periodic
+    ("turb3d", (5, 4, 6), 2, "dc", "emissivity", 10.0, "f64"),
+    ("adjoint2d", (9, 8, 1), 2, "plm", "emissivity", 5.0, "f64"),   # 2D Kerr-Schild, outflow
+    ("torus3d_big", (5, 4, 4), 1, "plm", "emissivity", 20.0, "f64"),  # polar with the pi shift, scattering
+    ("torus3d_big", (5, 4, 4), 1, "plm", "thermal", 20.0, "f64"),
+    ("turb3d", (6, 5, 7), 2, "plm", "emissivity", 3.0, "f32"),
+]
+
+
+@pytest.mark.parametrize("name,n,level,recon,coupling,C,prec", TAU_ADJ_CASES)
+def test_tau_weighted_step_vjp_matches_oracle(name, n, level, recon, coupling, C, prec):
+    """The adjoint with the optical-depth weighting of Sec. 2.4 against the
+    oracle's reverse mode: every output at 1e-11 (FP64; 2e-10 for the thermal
+    dL/dalpha_s as without the weighting) or 2e-4 (FP32), and the weighting's
+    own share of the opacity gradients (the difference from the unweighted
+    adjoint, run on both sides) at 1e-8 of its norm in FP64."""
+    w = _thermal_workload(name, n, level) if coupling == "thermal" else _emissivity_workload(name, n, level)
+    w = _moving(w)
+    st = oracle_setup(w)
+    gc = GpuCase(w)
+    try:
+        gmap = match_bins(gc.dir, st.ang.dir.numpy())
+        dt = OCFL.cfl_dt(st, w["cfl"])
+        rng = np.random.default_rng(12)
+        lam = rng.normal(size=w["I0"].shape)
+        lamT = rng.normal(size=w["T"].shape) if coupling == "thermal" else None
+        I0, T0 = torch.tensor(w["I0"]), torch.tensor(w["T"])
+        f64 = prec == "f64"
+        tdt = torch.float64 if f64 else torch.float32
+        out = {}
+        for CC in (C, 0.0):
+            lam_o, lamT_o, ga_o, gs_o, _ = OA.step_vjp(I0, T0, oracle_gas(w), dt, st,
+                                                       OS.Opts(recon=recon, mode=coupling, tau_const=CC),
+                                                       torch.tensor(lam),
+                                                       None if lamT is None else torch.tensor(lamT))
+            o = rad.rad_opts_default(precision=rad.RAD_F64 if f64 else rad.RAD_F32,
+                                     coupling=rad.RAD_COUPLE_THERMAL if coupling == "thermal"
+                                     else rad.RAD_COUPLE_EMISSIVITY,
+                                     recon=rad.RAD_RECON_PLM if recon == "plm" else rad.RAD_RECON_DC, tau_const=CC)
+            Ig = gc.to_gpu_I(w["I0"], gmap, tdt)
+            lg = gc.to_gpu_I(lam, gmap, tdt)
+            ln = torch.zeros_like(Ig)
+            gas = gc.gas(w)
+            lTg = None if lamT is None else torch.tensor(lamT, device="cuda")
+            lTn = None if lamT is None else torch.zeros_like(lTg)
+            ga = torch.zeros_like(gas["rho"])
+            gs = torch.zeros_like(ga)
+            ge = torch.zeros_like(ga) if coupling == "emissivity" else None
+            rad.rad_step_adjoint(gc.ctx, Ig, gas, dt, o, lg, ln, lTg, lTn, ga, gs, ge)
+            torch.cuda.synchronize()
+            rad.rad_check(gc.ctx)
+            out[CC] = (gc.from_gpu_I(ln.double(), gmap), ga.cpu().numpy(), gs.cpu().numpy(),
+                       lam_o.numpy(), ga_o.numpy(), gs_o.numpy(),
+                       None if lTn is None else (lTn.cpu().numpy(), lamT_o.numpy()))
+        lg_, ga_, gs_, lo_, gao, gso, lt = out[C]
+        tol = 1e-11 if f64 else 2e-4
+        assert rel_err(lg_, lo_) < tol
+        assert rel_err(ga_, gao) < tol
+        assert rel_err(gs_, gso) < (2e-10 if f64 and coupling == "thermal" else tol)
+        if lt is not None:
+            assert rel_err(lt[0], lt[1]) < tol
+        # the weighting's own share of the opacity gradients (FP64: in FP32 the
+        # share is below the rounding of the totals)
+        _, ga0, gs0, _, gao0, gso0, _ = out[0.0]
+        dgo = gao - gao0
+        assert np.abs(dgo).max() > 1e-4 * np.abs(gao).max()     # the weighting matters here
+        if f64:
+            assert rel_err(ga_ - ga0, dgo) < 1e-8
+            # thermal dL/dalpha_s: its conditioning (2.9e-11 of the total, see
+            # above) over the weighting's share (~2e-4 of it)
+            assert rel_err(gs_ - gs0, gso - gso0) < (1e-6 if coupling == "thermal" else 1e-8)
+    finally:
+        gc.close()
+

@@ -199,3 +199,48 @@ def test_thermal_step_vjp_dot_product(adj_case):
     lhs = float((lam * jI).sum() + (lamT * jT).sum())
     rhs = float((lam_n * dI).sum() + (lamT_n * dT).sum() + (g_aa * da).sum() + (g_as * ds).sum())
     assert abs(lhs - rhs) < 1e-12 * max(abs(lhs), 1.0)
+
+
+def test_tau_weighted_gradient_matches_central_differences(adj_case):
+    """With the optical-depth weighting of Sec. 2.4 the face factors depend on
+    alpha_E = alpha_a + alpha_s, so the opacity gradient has a second path
+    (through f = -expm1(-tau^2)).  Reverse-mode AD of the oracle against
+    central differences of its forward over two steps, on a moving gas (the
+    weighting acts only across velocity differences); the weighting changes
+    the gradient at the cells checked by far more than the tolerance, so a
+    dropped path fails."""
+    w, st, gas, dt = adj_case
+    rng = np.random.default_rng(21)
+    v = rng.uniform(-1, 1, gas["alpha_a"].shape + (3,))
+    v *= 0.3 / np.sqrt((v * v).sum(-1)).max()
+    g0 = dict(gas)
+    g0["u"] = torch.tensor(v / np.sqrt(1 - (v * v).sum(-1))[..., None])
+    opts = S.Opts(mode="emissivity", tau_const=5.0)
+    I0, T0 = torch.tensor(w["I0"]), torch.tensor(w["T"])
+    nsteps = 2
+    L, grads = A.gradient(I0, T0, g0, dt, st, opts, nsteps)
+    _, grads_free = A.gradient(I0, T0, g0, dt, st, S.Opts(mode="emissivity"), nsteps)
+
+    def loss_with(field, cell, h):
+        g2 = {k: (x.clone() if x is not None else None) for k, x in g0.items()}
+        g2[field][cell] += h
+        I, T = I0, T0
+        for _ in range(nsteps):
+            I, T, _, _ = S.rk2_step(I, T, g2, dt, st, opts)
+        return float(A.loss_outer(I, st))
+
+    for fi, field in enumerate(("alpha_a", "alpha_s")):
+        gmax = float(grads[fi].abs().max())
+        diff = (grads[fi] - grads_free[fi]).abs()
+        # the three cells where the weighting moves the gradient most, and two more
+        top = [tuple(int(x) for x in np.unravel_index(q, diff.shape)) for q in
+               torch.argsort(diff.flatten(), descending=True)[:3].tolist()]
+        for cell in top + [(0, 2, 4), (0, 3, 1)]:
+            ad = float(grads[fi][cell])
+            tol = 1e-6 * max(abs(ad), 2e-2 * gmax)
+            if cell in top:
+                assert float(diff[cell]) > 20 * tol, (field, cell)
+            h = 1e-5 * float(g0[field][cell])
+            fd = (loss_with(field, cell, h) - loss_with(field, cell, -h)) / (2 * h)
+            assert abs(fd - ad) <= tol, (field, cell, fd, ad)
+
