@@ -343,8 +343,6 @@ int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double d
   int st = check_opts(ctx, o);
   if (st != RAD_OK) return st;
   if ((st = check_gas(ctx, gas, o, true)) != RAD_OK) return st;
-  if (o->recon == RAD_RECON_PPM)
-    return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers DC and PLM reconstruction");
   if (o->rad_dom)
     return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers the coupling at the gas velocity (rad_dom = 0)");
   if (o->recon_ang != RAD_RECON_DC)

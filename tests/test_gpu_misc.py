@@ -122,11 +122,6 @@ def test_argument_errors_are_reported():
             rad.rad_step(ctx, I, gas, 0.1, rad.rad_opts_default(tau_const=-1.0))
         assert e.value.status == rad.RAD_EINVAL
         lam = torch.zeros_like(I)
-        with pytest.raises(rad.RadError) as e:     # the adjoint does not cover PPM
-            rad.rad_step_adjoint(ctx, I, gas, 0.01,
-                                 rad.rad_opts_default(coupling=rad.RAD_COUPLE_NONE, recon=rad.RAD_RECON_PPM),
-                                 lam, torch.zeros_like(I), None, None, f(1, 4, 4), f(1, 4, 4))
-        assert e.value.status == rad.RAD_EUNSUPPORTED
         with pytest.raises(rad.RadError) as e:     # unknown reconstruction
             rad.rad_step(ctx, I, gas, 0.01, rad.rad_opts_default(recon=7))
         assert e.value.status == rad.RAD_EINVAL
