@@ -182,7 +182,9 @@ __device__ __forceinline__ void edge_grad(bool plm, bool right, const R *w, R &p
 // Transposed transport of one stage (gather form, one thread per target bin).
 // PPM: the spatial reconstruction is PPM (each face state depends on the five
 // cells around its upwind cell) instead of DC / PLM (three cells).
-template <typename R, bool ANG, int MAXT, bool TAU, bool PPM>
+// AP (with ANG): PLM angular reconstruction along the lines of a
+// latitude-longitude grid instead of donor-cell angular fluxes.
+template <typename R, bool ANG, int MAXT, bool TAU, bool PPM, bool AP>
 __global__ void __launch_bounds__(MAXT, sizeof(R) == 8 ? 1 : 1280 / MAXT) k_transport_adj(AdjArgs A) {
   using Col = typename GeoTypes<R>::Col;
   using Face = typename GeoTypes<R>::Face;
@@ -261,10 +263,66 @@ __global__ void __launch_bounds__(MAXT, sizeof(R) == 8 ? 1 : 1280 / MAXT) k_tran
     }
     for (int t = 0; t < NM; ++t) ivd[2][t] = cg.invdV;
   }
+  // angular PLM (AP): the sides whose flux depends on this bin -- its own
+  // sides (it is the upwind or the downwind cell) and the sides whose upwind
+  // line reconstruction takes it as the cell behind -- with, per side, the
+  // prefactor P = len (V . nu) n_0 of Eq. flux_angle for this column, the
+  // cells p, q of the side and the upwind, downwind and behind cells
+  constexpr int NE = AP ? kMaxSlots + kMaxBehind : 1;
+  R ap_P[NE];
+  int ap_e[NE], ap_p[NE], ap_q[NE], ap_u[NE], ap_d[NE], ap_b[NE];
+  if (AP) {
+    auto edge_P = [&](int e, bool &upp) -> R {
+      const double *eg = a.edge_geo + 8 * e;
+      const R x = (R)eg[0], yv = (R)eg[1], z = (R)eg[2], len = (R)eg[6];
+      const R pr[10] = {R(1), x, yv, z, x * x, x * yv, x * z, yv * yv, yv * z, z * z};
+      R q0 = R(0), q1 = R(0), q2 = R(0);
+      for (int p = 0; p < 10; ++p) {
+        q0 += cg.K[0][p] * pr[p];
+        q1 += cg.K[1][p] * pr[p];
+        q2 += cg.K[2][p] * pr[p];
+      }
+      const R sp = -((R)eg[3] * q0 + (R)eg[4] * q1 + (R)eg[5] * q2);
+      upp = sp >= R(0);                       // upwind: p (ties to p, as the forward)
+      return len * sp * (cg.M[0][0] + cg.M[0][1] * x + cg.M[0][2] * yv + cg.M[0][3] * z);
+    };
+    for (int s = 0; s < NE; ++s) {
+      ap_P[s] = R(0);
+      ap_e[s] = -1;
+      ap_p[s] = ap_q[s] = ap_u[s] = ap_d[s] = ap_b[s] = nb_self;
+      int e = -1, side = -1;
+      if (s < kMaxSlots) {
+        if (act && a.slot_nbr[6 * n + s] >= 0) e = a.slot_edge[6 * n + s];
+      } else {
+        const int code = act ? a.line_behind[kMaxBehind * n + (s - kMaxSlots)] : -1;
+        if (code >= 0) {
+          e = code >> 1;
+          side = code & 1;
+        }
+      }
+      if (e < 0) continue;
+      bool upp;
+      const R P = edge_P(e, upp);
+      if (side >= 0 && upp != (side == 0)) continue;     // the reconstruction is from the other cell
+      const int p = a.edge_pq[2 * e], q = a.edge_pq[2 * e + 1];
+      ap_P[s] = P;
+      ap_e[s] = e;
+      ap_p[s] = p;
+      ap_q[s] = q;
+      ap_u[s] = upp ? p : q;
+      ap_d[s] = upp ? q : p;
+      ap_b[s] = a.edge_line[2 * e + (upp ? 0 : 1)];
+    }
+    // a side that is both one of this bin's own and one it is behind of
+    // (no lat/long grid has one) counts once
+    for (int s = kMaxSlots; s < NE; ++s)
+      for (int s2 = 0; s2 < kMaxSlots; ++s2)
+        if (ap_e[s] >= 0 && ap_e[s] == ap_e[s2]) ap_e[s] = -1;
+  }
   // angular: transposed coefficients
   R at_self = R(0), at_nb[kMaxSlots];
   int nb_m[kMaxSlots];
-  if (ANG) {
+  if (ANG && !AP) {
     R self = R(0);
     for (int s = 0; s < kMaxSlots; ++s) {
       at_nb[s] = R(0);
@@ -469,10 +527,23 @@ __global__ void __launch_bounds__(MAXT, sizeof(R) == 8 ? 1 : 1280 / MAXT) k_tran
         }
       }
     }
-    if (ANG) {
+    if (ANG && !AP) {
       R ga = at_self * mu0;
       for (int s = 0; s < kMaxSlots; ++s) ga += at_nb[s] * mu[addr(i, j, k, nb_m[s])];
       lam -= ga;
+    }
+    if (AP) {
+      // the side's flux F = P (I_u + q(I_b, I_u, I_d)) leaves p and enters q:
+      // d<mu, L>/dI = -P (mu_p / dOmega_p - mu_q / dOmega_q) dF/dI, through
+      // every role (behind, upwind, downwind) this bin plays on the side
+      for (int s = 0; s < NE; ++s) {
+        if (ap_e[s] < 0) continue;
+        const int p = ap_p[s], q = ap_q[s];
+        const R lphiA = -ap_P[s] * (mu[addr(i, j, k, p)] / (R)a.dOmega[p] - mu[addr(i, j, k, q)] / (R)a.dOmega[q]);
+        R d[3];
+        dphi(true, false, Il[addr(i, j, k, ap_b[s])], Il[addr(i, j, k, ap_u[s])], Il[addr(i, j, k, ap_d[s])], d);
+        lam += lphiA * ((ap_b[s] == n ? d[0] : R(0)) + (ap_u[s] == n ? d[1] : R(0)) + (ap_d[s] == n ? d[2] : R(0)));
+      }
     }
     if (tauw) {
       R gs[3];
@@ -523,25 +594,26 @@ __global__ void k_tau_grad(const double *gtau, int n1, int n2, int n3, int ndim,
 
 }  // namespace
 
-template <typename R, bool ANG, int MAXT>
+template <typename R, bool ANG, bool AP, int MAXT>
 void launch_tadj(const AdjArgs &A, bool tau, bool ppm, dim3 grid, int threads, cudaStream_t st) {
   if (ppm)
-    tau ? k_transport_adj<R, ANG, MAXT, true, true><<<grid, threads, 0, st>>>(A)
-        : k_transport_adj<R, ANG, MAXT, false, true><<<grid, threads, 0, st>>>(A);
+    tau ? k_transport_adj<R, ANG, MAXT, true, true, AP><<<grid, threads, 0, st>>>(A)
+        : k_transport_adj<R, ANG, MAXT, false, true, AP><<<grid, threads, 0, st>>>(A);
   else
-    tau ? k_transport_adj<R, ANG, MAXT, true, false><<<grid, threads, 0, st>>>(A)
-        : k_transport_adj<R, ANG, MAXT, false, false><<<grid, threads, 0, st>>>(A);
+    tau ? k_transport_adj<R, ANG, MAXT, true, false, AP><<<grid, threads, 0, st>>>(A)
+        : k_transport_adj<R, ANG, MAXT, false, false, AP><<<grid, threads, 0, st>>>(A);
 }
 
-template <typename R, bool ANG>
+// AP: angular PLM on a latitude-longitude grid (curved space only)
+template <typename R, bool ANG, bool AP = false>
 cudaError_t launch_transport_adj(const AdjArgs &A, cudaStream_t st) {
   int threads = (A.s.nap + 31) / 32 * 32;
   int nchunk = (A.s.n3 + A.s.kc - 1) / A.s.kc;
   dim3 grid((unsigned)((long long)A.s.n1 * A.s.n2 * nchunk));
   const bool tau = A.s.tau_const > 0.0, ppm = A.s.recon == RAD_RECON_PPM;
-  if (threads <= 256) launch_tadj<R, ANG, 256>(A, tau, ppm, grid, threads, st);
-  else if (threads <= 512) launch_tadj<R, ANG, 512>(A, tau, ppm, grid, threads, st);
-  else launch_tadj<R, ANG, 1024>(A, tau, ppm, grid, threads, st);
+  if (threads <= 256) launch_tadj<R, ANG, AP, 256>(A, tau, ppm, grid, threads, st);
+  else if (threads <= 512) launch_tadj<R, ANG, AP, 512>(A, tau, ppm, grid, threads, st);
+  else launch_tadj<R, ANG, AP, 1024>(A, tau, ppm, grid, threads, st);
   if (tau) {
     const StageArgs &a = A.s;
     const long long ncell = (long long)a.n1 * a.n2 * a.n3;
@@ -552,10 +624,12 @@ cudaError_t launch_transport_adj(const AdjArgs &A, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Explicitly instantiated in adjoint_tadj_<precision>_<flat|ang>.cu.
+// Explicitly instantiated in adjoint_tadj_<precision>_<flat|ang|angplm>.cu.
 extern template cudaError_t launch_transport_adj<float, false>(const AdjArgs &, cudaStream_t);
 extern template cudaError_t launch_transport_adj<float, true>(const AdjArgs &, cudaStream_t);
 extern template cudaError_t launch_transport_adj<double, false>(const AdjArgs &, cudaStream_t);
 extern template cudaError_t launch_transport_adj<double, true>(const AdjArgs &, cudaStream_t);
+extern template cudaError_t launch_transport_adj<float, true, true>(const AdjArgs &, cudaStream_t);
+extern template cudaError_t launch_transport_adj<double, true, true>(const AdjArgs &, cudaStream_t);
 
 }  // namespace rad

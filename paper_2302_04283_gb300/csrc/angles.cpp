@@ -333,6 +333,19 @@ bool build_latlong(int n_zeta, int n_psi, AngleGrid &g, std::string &err) {
       g.slot_edge[6 * n + s] = nb[n][s].second;
     }
   }
+  // the inverse of edge_line: per bin, the sides whose line reconstruction
+  // (from p, or from q) takes it as the cell behind
+  g.line_behind.assign(kMaxBehind * g.n_ang, -1);
+  std::vector<int> cnt(g.n_ang, 0);
+  for (int e = 0; e < g.n_edge; ++e)
+    for (int s = 0; s < 2; ++s) {
+      const int t = g.edge_line[2 * e + s];
+      if (cnt[t] == kMaxBehind) {
+        err = "lat/long cell behind more than four sides";
+        return false;
+      }
+      g.line_behind[kMaxBehind * t + cnt[t]++] = 2 * e + s;
+    }
   return pi_rotation_perm(g, err);
 }
 

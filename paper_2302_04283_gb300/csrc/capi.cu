@@ -24,6 +24,7 @@ void free_angles(rad::DevAngles &d) {
   cudaFree(d.edge_geo);
   cudaFree(d.edge_pq);
   cudaFree(d.edge_line);
+  cudaFree(d.line_behind);
   d = rad::DevAngles();
 }
 
@@ -111,6 +112,8 @@ static int install_angles(rad_ctx *ctx, AngleGrid &g, int *n_ang_out, int *n_ang
   // device tables, padded to n_ap bins with zero directions / solid angles
   std::vector<double> dir(3 * g.n_ap, 0.0), dOm(g.n_ap, 0.0), egeo(8 * g.n_edge, 0.0);
   std::vector<int> snb(6 * g.n_ap, -1), sed(6 * g.n_ap, -1), perm(g.n_ap, 0);
+  std::vector<int> lbh(g.line_behind.empty() ? 0 : rad::kMaxBehind * g.n_ap, -1);   // padded bins: none
+  for (size_t q = 0; q < g.line_behind.size(); ++q) lbh[q] = g.line_behind[q];
   for (int n = 0; n < g.n_ang; ++n) {
     for (int a = 0; a < 3; ++a) dir[3 * n + a] = g.dir[3 * n + a];
     dOm[n] = g.dOmega[n];
@@ -136,7 +139,8 @@ static int install_angles(rad_ctx *ctx, AngleGrid &g, int *n_ang_out, int *n_ang
       (ce = upload(&ctx->dang.perm, perm, ctx->stream)) != cudaSuccess ||
       (ce = upload(&ctx->dang.edge_geo, egeo, ctx->stream)) != cudaSuccess ||
       (ce = upload(&ctx->dang.edge_pq, g.edge_pq, ctx->stream)) != cudaSuccess ||
-      (!g.edge_line.empty() && (ce = upload(&ctx->dang.edge_line, g.edge_line, ctx->stream)) != cudaSuccess)) {
+      (!g.edge_line.empty() && (ce = upload(&ctx->dang.edge_line, g.edge_line, ctx->stream)) != cudaSuccess) ||
+      (!lbh.empty() && (ce = upload(&ctx->dang.line_behind, lbh, ctx->stream)) != cudaSuccess)) {
     free_angles(ctx->dang);
     return fail(ctx, RAD_ENOMEM, std::string("angle table upload failed: ") + cudaGetErrorString(ce));
   }
@@ -345,8 +349,6 @@ int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double d
   if ((st = check_gas(ctx, gas, o, true)) != RAD_OK) return st;
   if (o->rad_dom)
     return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers the coupling at the gas velocity (rad_dom = 0)");
-  if (o->recon_ang != RAD_RECON_DC)
-    return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers donor-cell angular fluxes (recon_ang = RAD_RECON_DC)");
   if (!I_n || !lam_np1 || !lam_n || !g_aa || !g_as) return fail(ctx, RAD_EINVAL, "null argument");
   if (!(dt > 0.0)) return fail(ctx, RAD_EINVAL, "dt must be > 0");
   if (ctx->ang.n_ang > rad::kMaxBinsStep)

@@ -15,6 +15,8 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxBinsStep = 812;        // rad_step: one CTA of <= 512 threads holds all bins of a cell
                                          // (812 = geodesic level 9)
 constexpr int kMaxSlots = 6;             // neighbours of a geodesic cell
+constexpr int kMaxBehind = 4;            // sides whose line reconstruction reads a lat/long cell as
+                                         // the cell behind (one per line direction)
 
 // error bits of the sticky device word (bit k <-> status -k)
 constexpr int kErrNoConv = 1 << 4;       // RAD_ENOCONV = -4
@@ -34,6 +36,9 @@ struct AngleGrid {
   std::vector<int> perm;          // [n_ang] bin of the pi-rotation about 2hat
   std::vector<int> edge_line;     // [n_edge][2] cell behind p, cell beyond q on the line through the
                                   // side (latitude-longitude grids; empty for the geodesic grid)
+  std::vector<int> line_behind;   // [n_ang][kMaxBehind] 2 e + s for every side e whose line
+                                  // reconstruction from its cell s (0: p, 1: q) takes this bin as
+                                  // the cell behind (-1 pad; latitude-longitude grids only)
 };
 
 bool build_geodesic(int level, AngleGrid &g, std::string &err);
@@ -82,6 +87,7 @@ struct DevAngles {
   double *edge_geo = nullptr;  // [n_edge][8]: mid xyz, nrm xyz, len, p-index
   int *edge_pq = nullptr;      // [n_edge][2]
   int *edge_line = nullptr;    // [n_edge][2] (latitude-longitude grids only)
+  int *line_behind = nullptr;  // [n_ap][kMaxBehind] (latitude-longitude grids only)
 };
 
 struct DevGeom {

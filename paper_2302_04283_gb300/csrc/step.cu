@@ -140,6 +140,7 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
   a.slot_edge = ctx->dang.slot_edge;
   a.edge_pq = ctx->dang.edge_pq;
   a.edge_line = ctx->dang.edge_line;
+  a.line_behind = ctx->dang.line_behind;
   a.recon_ang = o->recon_ang;
   a.recon = o->recon;
   a.mode = o->coupling;

@@ -72,6 +72,7 @@ struct StageArgs {
   const double *dir, *dOmega, *edge_geo;
   const int *perm, *slot_nbr, *slot_edge, *edge_pq;
   const int *edge_line;    // latitude-longitude grids: cell behind p, cell beyond q of each side
+  const int *line_behind;  // latitude-longitude grids: per bin, the sides it is the cell behind of (adjoint)
   int recon_ang;           // RAD_RECON_DC or RAD_RECON_PLM (angular fluxes)
   int recon, mode, zero_guard;
   double n0crit, a_rad, gamma;
