@@ -283,9 +283,10 @@ int rad_step_host(rad_ctx *ctx, int n_items, const rad_host_item *items, double 
  * the stages; with RAD_COUPLE_EMISSIVITY or RAD_COUPLE_NONE the temperature
  * is frozen and lamT_n = lamT_np1.  With opts->tau_const > 0 (the
  * optical-depth weighting of Sec. 2.4) the opacity gradients include the
- * path through the face weights.  Any spatial reconstruction (DC, PLM, PPM;
- * the limiters differentiated on their active branches); rad_dom must be 0
- * and recon_ang DC (RAD_EUNSUPPORTED otherwise).  lam arrays use the intensity
+ * path through the face weights.  Any spatial reconstruction (DC, PLM, PPM)
+ * and either angular one (DC, or PLM along the lines of a latitude-longitude
+ * grid), the limiters differentiated on their active branches; rad_dom must
+ * be 0 (RAD_EUNSUPPORTED otherwise).  lam arrays use the intensity
  * layout and precision; lamT arrays are device FP64 [k][j][i].  lamT_np1 may
  * be NULL (zero), lamT_n may be NULL (not written) and may equal lamT_np1;
  * g_eta may be NULL.
