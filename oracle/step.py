@@ -36,6 +36,7 @@ class Opts:
     tau_const: float = 0.0      # C of the optical-depth flux weighting (0: free streaming)
     rad_dom: bool = False       # radiation-dominated velocity substitution (Sec. 2.5)
     recon_ang: str = "dc"       # 'dc' | 'plm' (PLM along the lines of a latitude-longitude grid)
+                                # | 'mapr' (minimum-angle planes on a geodesic grid)
 
 
 def operator_L(I, setup, opts, tau=None):

@@ -12,6 +12,7 @@ every flux dimension (Sec. 2 task list, "apply boundary conditions").
 """
 import math
 
+import numpy as np
 import torch
 
 from . import DTYPE
@@ -365,17 +366,92 @@ def angular_speeds(setup):
     return ang.edge_len * s * n0, s
 
 
+def mapr_stencils(ang):
+    """Per cell c of a geodesic grid, the geometry of its minimum-angle plane
+    reconstruction: its neighbours in cyclic order around n_c, their
+    gnomonic coordinates x = (v . t1, v . t2) / (v . n_c) in the tangent
+    plane at n_c (t1, t2 any orthonormal pair normal to n_c), and the
+    gnomonic coordinates of the midpoints of its sides.  Returns a list of
+    (neighbours, X [K, 2], {neighbour: (side, x_side)})."""
+    if getattr(ang, "_mapr", None) is not None:
+        return ang._mapr
+    dirs = ang.dir.numpy()
+    mids = ang.edge_mid.numpy()
+    side = {}
+    for e, (p, q) in enumerate(ang.edges.tolist()):
+        side[(p, q)] = e
+        side[(q, p)] = e
+    out = []
+    for c in range(ang.n_ang):
+        n = dirs[c]
+        t1 = np.cross(n, [0.3, 0.5, 0.7])
+        t1 /= np.linalg.norm(t1)
+        t2 = np.cross(n, t1)
+
+        def gn(v):
+            return np.array([v @ t1, v @ t2]) / (v @ n)
+
+        nb = sorted(ang.nbr[c], key=lambda m: math.atan2(dirs[m] @ t2, dirs[m] @ t1))
+        X = np.array([gn(dirs[m]) for m in nb])
+        xs = {m: (side[(c, m)], gn(mids[side[(c, m)]])) for m in nb}
+        out.append((nb, X, xs))
+    ang._mapr = out
+    return out
+
+
+def mapr_face_values(I, ang):
+    """Upwind candidates at every side p | q by minimum-angle plane
+    reconstruction (MAPR), which the paper names for geodesic grids (Sec.
+    2.6) without stating it.  Reading: around cell c every two cyclically
+    adjacent neighbours a, b fix a plane through (0, I_c), (x_a, I_a),
+    (x_b, I_b) in c's gnomonic tangent plane, i.e. a gradient g with
+    g . x_a = I_a - I_c and g . x_b = I_b - I_c; the least inclined plane
+    (smallest |g|; the first in cyclic order on a tie) is kept, and c's value
+    at a side is I_c + g . x_side."""
+    st = mapr_stencils(ang)
+    n_edge = ang.edges.shape[0]
+    vals = [[None, None] for _ in range(n_edge)]
+    for c, (nb, X, xs) in enumerate(st):
+        Ic = I[..., c]
+        K = len(nb)
+        best_g = best_q = None
+        for a in range(K):
+            b = (a + 1) % K
+            M = torch.tensor(np.array([X[a], X[b]]), dtype=I.dtype)
+            d = torch.stack([I[..., nb[a]] - Ic, I[..., nb[b]] - Ic], -1)
+            g = torch.linalg.solve(M, d.unsqueeze(-1)).squeeze(-1)      # M g = d
+            q = (g * g).sum(-1)
+            if best_g is None:
+                best_g, best_q = g, q
+            else:
+                take = q < best_q
+                best_g = torch.where(take[..., None], g, best_g)
+                best_q = torch.where(take, q, best_q)
+        for m in nb:
+            e, xe = xs[m]
+            v = Ic + (best_g * torch.tensor(xe, dtype=I.dtype)).sum(-1)
+            vals[e][0 if int(ang.edges[e, 0]) == c else 1] = v
+    Fp = torch.stack([v[0] for v in vals], -1)
+    Fq = torch.stack([v[1] for v in vals], -1)
+    return Fp, Fq
+
+
 def angular_face_values(I, ang, recon_ang="dc"):
     """Upwind candidates at every side p | q: (value from p, value from q).
 
     DC: the cell values.  PLM (latitude-longitude grids, Sec. 2.6): the
     spatial reconstruction applied along the line through p and q, i.e.
     I_p + van_leer(I_p - I_behind, I_q - I_p) / 2 from p and
-    I_q + van_leer(I_q - I_beyond, I_p - I_q) / 2 from q."""
+    I_q + van_leer(I_q - I_beyond, I_p - I_q) / 2 from q.  MAPR (geodesic
+    grids): mapr_face_values."""
     p, q = ang.edges[:, 0], ang.edges[:, 1]
     Ip, Iq = I[..., p], I[..., q]
     if recon_ang == "dc":
         return Ip, Iq
+    if recon_ang == "mapr":
+        if hasattr(ang, "edge_line"):
+            raise ValueError("MAPR is defined here for geodesic grids")
+        return mapr_face_values(I, ang)
     if recon_ang != "plm" or not hasattr(ang, "edge_line"):
         raise ValueError("angular PLM needs a latitude-longitude grid")
     Ib, If = I[..., ang.edge_line[:, 0]], I[..., ang.edge_line[:, 1]]
