@@ -62,7 +62,7 @@ typedef enum {
 enum { RAD_MINK_CART = 0, RAD_MINK_SPH = 1, RAD_KS_SPH = 2 };
 enum { RAD_BC_PERIODIC = 0, RAD_BC_OUTFLOW = 1, RAD_BC_POLAR = 2 };
 enum { RAD_F64 = 0, RAD_F32 = 1 };
-enum { RAD_RECON_DC = 0, RAD_RECON_PLM = 1, RAD_RECON_PPM = 2 };
+enum { RAD_RECON_DC = 0, RAD_RECON_PLM = 1, RAD_RECON_PPM = 2, RAD_RECON_MAPR = 3 /* angular only */ };
 enum { RAD_COUPLE_THERMAL = 0, RAD_COUPLE_EMISSIVITY = 1, RAD_COUPLE_NONE = 2 };
 enum { RAD_FRAME_TETRAD = 0, RAD_FRAME_COORD = 1, RAD_FRAME_FLUID = 2 };
 enum { RAD_MOM_SIMT = 0, RAD_MOM_BF16X3 = 1 };
@@ -175,12 +175,19 @@ typedef struct {
                         transport and the coupling as two kernels.  Default 0;
                         rad_step_adjoint requires 0. */
   int recon_ang;     /* angular reconstruction: RAD_RECON_DC (default; the
-                        geodesic grid's scheme, Sec. 2.6) or RAD_RECON_PLM:
+                        geodesic grid's scheme, Sec. 2.6), RAD_RECON_PLM:
                         the spatial PLM applied along the lines of a
                         latitude-longitude grid (bands along a side of
                         constant psi, sectors through both poles for a
                         side of constant zeta; RAD_EUNSUPPORTED on a
-                        geodesic grid).  rad_step_adjoint requires DC. */
+                        geodesic grid), or RAD_RECON_MAPR: minimum-angle
+                        plane reconstruction on a geodesic grid (Sec. 2.6
+                        names it; here each bin keeps the least inclined of
+                        the planes through itself and two cyclically
+                        adjacent neighbours in its gnomonic tangent plane,
+                        evaluated at the side midpoints; RAD_EUNSUPPORTED on
+                        a latitude-longitude grid).  rad_step_adjoint takes
+                        DC or PLM. */
 } rad_opts;
 
 /* Fill *opts with the defaults above (FP64, PLM, thermal coupling). */

@@ -23,7 +23,7 @@ RAD_OK, RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA, RAD_ENOCONV, RAD_ENONFINITE, RAD_ESTA
 RAD_MINK_CART, RAD_MINK_SPH, RAD_KS_SPH = 0, 1, 2
 RAD_BC_PERIODIC, RAD_BC_OUTFLOW, RAD_BC_POLAR = 0, 1, 2
 RAD_F64, RAD_F32 = 0, 1
-RAD_RECON_DC, RAD_RECON_PLM, RAD_RECON_PPM = 0, 1, 2
+RAD_RECON_DC, RAD_RECON_PLM, RAD_RECON_PPM, RAD_RECON_MAPR = 0, 1, 2, 3
 RAD_COUPLE_THERMAL, RAD_COUPLE_EMISSIVITY, RAD_COUPLE_NONE = 0, 1, 2
 RAD_FRAME_TETRAD, RAD_FRAME_COORD, RAD_FRAME_FLUID = 0, 1, 2
 RAD_MOM_SIMT, RAD_MOM_BF16X3 = 0, 1

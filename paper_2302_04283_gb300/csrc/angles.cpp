@@ -81,6 +81,65 @@ bool pi_rotation_perm(AngleGrid &g, std::string &err) {
 
 }  // namespace
 
+// Minimum-angle plane reconstruction on a geodesic grid: per cell its
+// neighbours in cyclic order around n, for each two cyclically adjacent ones
+// (a, b) the inverse of [x_a; x_b] (gnomonic coordinates x = (v . t1,
+// v . t2) / (v . n) in the tangent plane at n, any orthonormal t1, t2), so
+// that the plane's gradient is g = inv (I_a - I_c, I_b - I_c); and per slot
+// the gnomonic coordinates of the side's midpoint in this cell's and in the
+// neighbour's tangent plane.
+static void build_mapr(AngleGrid &g, const std::vector<V3> &dir) {
+  const int n_ang = g.n_ang;
+  std::vector<V3> t1(n_ang), t2(n_ang);
+  for (int c = 0; c < n_ang; ++c) {
+    const V3 n = dir[c];
+    const V3 a = std::fabs(n.z) < 0.9 ? V3{0.0, 0.0, 1.0} : V3{1.0, 0.0, 0.0};
+    t1[c] = unit(cross(n, a));
+    t2[c] = cross(n, t1[c]);
+  }
+  auto gn = [&](int c, V3 v, double &x, double &y) {
+    const double w = dot(v, dir[c]);
+    x = dot(v, t1[c]) / w;
+    y = dot(v, t2[c]) / w;
+  };
+  g.mapr_nb.assign(6 * n_ang, -1);
+  g.mapr_minv.assign(24 * n_ang, 0.0);
+  g.mapr_xo.assign(12 * n_ang, 0.0);
+  g.mapr_xn.assign(12 * n_ang, 0.0);
+  for (int c = 0; c < n_ang; ++c) {
+    std::vector<std::pair<double, int>> cyc;
+    for (int s = 0; s < 6; ++s) {
+      const int m = g.nbr[6 * c + s];
+      if (m < 0) continue;
+      double x, y;
+      gn(c, dir[m], x, y);
+      cyc.push_back({std::atan2(y, x), m});
+    }
+    std::sort(cyc.begin(), cyc.end());
+    const int K = (int)cyc.size();
+    for (int a = 0; a < K; ++a) g.mapr_nb[6 * c + a] = cyc[a].second;
+    for (int a = 0; a < K; ++a) {
+      double xa, ya, xb, yb;
+      gn(c, dir[cyc[a].second], xa, ya);
+      gn(c, dir[cyc[(a + 1) % K].second], xb, yb);
+      const double det = xa * yb - ya * xb;           // rows (xa, ya), (xb, yb)
+      double *mi = &g.mapr_minv[24 * c + 4 * a];
+      mi[0] = yb / det;
+      mi[1] = -ya / det;
+      mi[2] = -xb / det;
+      mi[3] = xa / det;
+    }
+    for (int s = 0; s < 6; ++s) {
+      const int m = g.nbr[6 * c + s];
+      if (m < 0) continue;
+      const int e = g.slot_edge[6 * c + s];
+      const V3 mid{g.edge_mid[3 * e], g.edge_mid[3 * e + 1], g.edge_mid[3 * e + 2]};
+      gn(c, mid, g.mapr_xo[12 * c + 2 * s], g.mapr_xo[12 * c + 2 * s + 1]);
+      gn(m, mid, g.mapr_xn[12 * c + 2 * s], g.mapr_xn[12 * c + 2 * s + 1]);
+    }
+  }
+}
+
 bool build_geodesic(int N, AngleGrid &g, std::string &err) {
   if (N < 1 || N > 32) {
     err = "geodesic level must be in [1, 32]";
@@ -232,6 +291,7 @@ bool build_geodesic(int N, AngleGrid &g, std::string &err) {
       g.slot_edge[6 * n + s] = nb[n][s].second;
     }
   }
+  build_mapr(g, dir);
   return pi_rotation_perm(g, err);
 }
 

@@ -25,6 +25,10 @@ void free_angles(rad::DevAngles &d) {
   cudaFree(d.edge_pq);
   cudaFree(d.edge_line);
   cudaFree(d.line_behind);
+  cudaFree(d.mapr_nb);
+  cudaFree(d.mapr_minv);
+  cudaFree(d.mapr_xo);
+  cudaFree(d.mapr_xn);
   d = rad::DevAngles();
 }
 
@@ -114,6 +118,15 @@ static int install_angles(rad_ctx *ctx, AngleGrid &g, int *n_ang_out, int *n_ang
   std::vector<int> snb(6 * g.n_ap, -1), sed(6 * g.n_ap, -1), perm(g.n_ap, 0);
   std::vector<int> lbh(g.line_behind.empty() ? 0 : rad::kMaxBehind * g.n_ap, -1);   // padded bins: none
   for (size_t q = 0; q < g.line_behind.size(); ++q) lbh[q] = g.line_behind[q];
+  // minimum-angle plane tables, padded to n_ap bins (padding: no neighbours)
+  const bool mapr = !g.mapr_nb.empty();
+  std::vector<int> mnb(mapr ? 6 * g.n_ap : 0, -1);
+  std::vector<double> mminv(mapr ? 24 * g.n_ap : 0, 0.0), mxo(mapr ? 12 * g.n_ap : 0, 0.0),
+      mxn(mapr ? 12 * g.n_ap : 0, 0.0);
+  for (size_t q = 0; q < g.mapr_nb.size(); ++q) mnb[q] = g.mapr_nb[q];
+  for (size_t q = 0; q < g.mapr_minv.size(); ++q) mminv[q] = g.mapr_minv[q];
+  for (size_t q = 0; q < g.mapr_xo.size(); ++q) mxo[q] = g.mapr_xo[q];
+  for (size_t q = 0; q < g.mapr_xn.size(); ++q) mxn[q] = g.mapr_xn[q];
   for (int n = 0; n < g.n_ang; ++n) {
     for (int a = 0; a < 3; ++a) dir[3 * n + a] = g.dir[3 * n + a];
     dOm[n] = g.dOmega[n];
@@ -140,7 +153,11 @@ static int install_angles(rad_ctx *ctx, AngleGrid &g, int *n_ang_out, int *n_ang
       (ce = upload(&ctx->dang.edge_geo, egeo, ctx->stream)) != cudaSuccess ||
       (ce = upload(&ctx->dang.edge_pq, g.edge_pq, ctx->stream)) != cudaSuccess ||
       (!g.edge_line.empty() && (ce = upload(&ctx->dang.edge_line, g.edge_line, ctx->stream)) != cudaSuccess) ||
-      (!lbh.empty() && (ce = upload(&ctx->dang.line_behind, lbh, ctx->stream)) != cudaSuccess)) {
+      (!lbh.empty() && (ce = upload(&ctx->dang.line_behind, lbh, ctx->stream)) != cudaSuccess) ||
+      (mapr && ((ce = upload(&ctx->dang.mapr_nb, mnb, ctx->stream)) != cudaSuccess ||
+                (ce = upload(&ctx->dang.mapr_minv, mminv, ctx->stream)) != cudaSuccess ||
+                (ce = upload(&ctx->dang.mapr_xo, mxo, ctx->stream)) != cudaSuccess ||
+                (ce = upload(&ctx->dang.mapr_xn, mxn, ctx->stream)) != cudaSuccess))) {
     free_angles(ctx->dang);
     return fail(ctx, RAD_ENOMEM, std::string("angle table upload failed: ") + cudaGetErrorString(ce));
   }
@@ -277,9 +294,12 @@ static int check_opts(rad_ctx *ctx, const rad_opts *o) {
   if (!(o->tau_const >= 0.0) || !std::isfinite(o->tau_const))
     return fail(ctx, RAD_EINVAL, "tau_const must be finite and >= 0");
   if (o->rad_dom != 0 && o->rad_dom != 1) return fail(ctx, RAD_EINVAL, "rad_dom must be 0 or 1");
-  if (o->recon_ang != RAD_RECON_DC && o->recon_ang != RAD_RECON_PLM) return fail(ctx, RAD_EINVAL, "bad recon_ang");
+  if (o->recon_ang != RAD_RECON_DC && o->recon_ang != RAD_RECON_PLM && o->recon_ang != RAD_RECON_MAPR)
+    return fail(ctx, RAD_EINVAL, "bad recon_ang");
   if (o->recon_ang == RAD_RECON_PLM && ctx->ang.edge_line.empty())
     return fail(ctx, RAD_EUNSUPPORTED, "angular PLM needs a latitude-longitude grid (rad_init_angles_latlong)");
+  if (o->recon_ang == RAD_RECON_MAPR && ctx->ang.mapr_nb.empty())
+    return fail(ctx, RAD_EUNSUPPORTED, "MAPR needs a geodesic grid (rad_init_angles)");
   if (o->rad_dom && o->coupling != RAD_COUPLE_THERMAL)
     return fail(ctx, RAD_EINVAL, "rad_dom applies to the thermal coupling");
   return RAD_OK;
@@ -349,6 +369,8 @@ int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double d
   if ((st = check_gas(ctx, gas, o, true)) != RAD_OK) return st;
   if (o->rad_dom)
     return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers the coupling at the gas velocity (rad_dom = 0)");
+  if (o->recon_ang == RAD_RECON_MAPR)
+    return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers donor-cell and line-PLM angular fluxes");
   if (!I_n || !lam_np1 || !lam_n || !g_aa || !g_as) return fail(ctx, RAD_EINVAL, "null argument");
   if (!(dt > 0.0)) return fail(ctx, RAD_EINVAL, "dt must be > 0");
   if (ctx->ang.n_ang > rad::kMaxBinsStep)

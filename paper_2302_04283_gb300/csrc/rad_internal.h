@@ -36,6 +36,10 @@ struct AngleGrid {
   std::vector<int> perm;          // [n_ang] bin of the pi-rotation about 2hat
   std::vector<int> edge_line;     // [n_edge][2] cell behind p, cell beyond q on the line through the
                                   // side (latitude-longitude grids; empty for the geodesic grid)
+  std::vector<int> mapr_nb;       // [n_ang][6] neighbours in cyclic order (-1 pad; geodesic grids)
+  std::vector<double> mapr_minv;  // [n_ang][6][4] inverse of [x_a; x_b] of plane a (gnomonic x)
+  std::vector<double> mapr_xo;    // [n_ang][6][2] gnomonic x of slot s's side midpoint, own plane
+  std::vector<double> mapr_xn;    // [n_ang][6][2] the same midpoint in the neighbour's plane
   std::vector<int> line_behind;   // [n_ang][kMaxBehind] 2 e + s for every side e whose line
                                   // reconstruction from its cell s (0: p, 1: q) takes this bin as
                                   // the cell behind (-1 pad; latitude-longitude grids only)
@@ -88,6 +92,10 @@ struct DevAngles {
   int *edge_pq = nullptr;      // [n_edge][2]
   int *edge_line = nullptr;    // [n_edge][2] (latitude-longitude grids only)
   int *line_behind = nullptr;  // [n_ap][kMaxBehind] (latitude-longitude grids only)
+  int *mapr_nb = nullptr;      // [n_ap][6] (geodesic grids only)
+  double *mapr_minv = nullptr; // [n_ap][6][4]
+  double *mapr_xo = nullptr;   // [n_ap][6][2]
+  double *mapr_xn = nullptr;   // [n_ap][6][2]
 };
 
 struct DevGeom {

@@ -4,6 +4,6 @@
 
 namespace rad {
 
-template cudaError_t launch_stage_rp<float, true, false, kNapGeo8>(const StageArgs &a, cudaStream_t st);
+template cudaError_t launch_stage_rp<float, true, 0, kNapGeo8>(const StageArgs &a, cudaStream_t st);
 
 }  // namespace rad

@@ -4,6 +4,6 @@
 
 namespace rad {
 
-template cudaError_t launch_stage_rp<float, false, false, kNapGeo4>(const StageArgs &a, cudaStream_t st);
+template cudaError_t launch_stage_rp<float, false, 0, kNapGeo4>(const StageArgs &a, cudaStream_t st);
 
 }  // namespace rad

@@ -4,6 +4,6 @@
 
 namespace rad {
 
-template cudaError_t launch_stage_rp<double, true, true>(const StageArgs &a, cudaStream_t st);
+template cudaError_t launch_stage_rp<double, true, 1>(const StageArgs &a, cudaStream_t st);
 
 }  // namespace rad

@@ -8,10 +8,10 @@
 
 namespace rad {
 
-template <typename R, bool ANG, int RC, bool ST2, bool TAU, bool AP, int NAP>
+template <typename R, bool ANG, int RC, bool ST2, bool TAU, int AR, int NAP>
 cudaError_t launch_stage_t(const StageArgs &a, int threads, dim3 grid, cudaStream_t st) {
-  size_t smem = stage_smem<R, ANG>(threads, a.nap, a.kc, a.depth, TAU, stage_rows(RC));
-  auto kern = k_stage<R, ANG, RC, ST2, TAU, AP, NAP>;
+  size_t smem = stage_smem<R, ANG>(threads, a.nap, a.kc, a.depth, TAU, stage_rows(RC), AR == 2);
+  auto kern = k_stage<R, ANG, RC, ST2, TAU, AR, NAP>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -22,26 +22,26 @@ cudaError_t launch_stage_t(const StageArgs &a, int threads, dim3 grid, cudaStrea
   return cudaGetLastError();
 }
 
-template <typename R, bool ANG, bool TAU, bool AP, int NAP>
+template <typename R, bool ANG, bool TAU, int AR, int NAP>
 cudaError_t launch_stage_pt(const StageArgs &a, int threads, dim3 grid, cudaStream_t st) {
   if (a.recon == RAD_RECON_PPM)
-    return a.stage2 ? launch_stage_t<R, ANG, RAD_RECON_PPM, true, TAU, AP, NAP>(a, threads, grid, st)
-                    : launch_stage_t<R, ANG, RAD_RECON_PPM, false, TAU, AP, NAP>(a, threads, grid, st);
+    return a.stage2 ? launch_stage_t<R, ANG, RAD_RECON_PPM, true, TAU, AR, NAP>(a, threads, grid, st)
+                    : launch_stage_t<R, ANG, RAD_RECON_PPM, false, TAU, AR, NAP>(a, threads, grid, st);
   if (a.recon == RAD_RECON_PLM)
-    return a.stage2 ? launch_stage_t<R, ANG, RAD_RECON_PLM, true, TAU, AP, NAP>(a, threads, grid, st)
-                    : launch_stage_t<R, ANG, RAD_RECON_PLM, false, TAU, AP, NAP>(a, threads, grid, st);
-  return a.stage2 ? launch_stage_t<R, ANG, RAD_RECON_DC, true, TAU, AP, NAP>(a, threads, grid, st)
-                  : launch_stage_t<R, ANG, RAD_RECON_DC, false, TAU, AP, NAP>(a, threads, grid, st);
+    return a.stage2 ? launch_stage_t<R, ANG, RAD_RECON_PLM, true, TAU, AR, NAP>(a, threads, grid, st)
+                    : launch_stage_t<R, ANG, RAD_RECON_PLM, false, TAU, AR, NAP>(a, threads, grid, st);
+  return a.stage2 ? launch_stage_t<R, ANG, RAD_RECON_DC, true, TAU, AR, NAP>(a, threads, grid, st)
+                  : launch_stage_t<R, ANG, RAD_RECON_DC, false, TAU, AR, NAP>(a, threads, grid, st);
 }
 
-template <typename R, bool ANG, bool AP, int NAP>
+template <typename R, bool ANG, int AR, int NAP>
 cudaError_t launch_stage_rp(const StageArgs &a, cudaStream_t st) {
   if (NAP > 0 && a.nap != NAP) return cudaErrorInvalidValue;
   const int threads = (a.nap / 2 + 31) / 32 * 32;     // two bins per consumer thread
   const int nchunk = (a.n3 + a.kc - 1) / a.kc;
   const dim3 grid((unsigned)((long long)a.n1 * a.n2 * nchunk));
-  return a.tau_const > 0.0 ? launch_stage_pt<R, ANG, true, AP, NAP>(a, threads, grid, st)
-                           : launch_stage_pt<R, ANG, false, AP, NAP>(a, threads, grid, st);
+  return a.tau_const > 0.0 ? launch_stage_pt<R, ANG, true, AR, NAP>(a, threads, grid, st)
+                           : launch_stage_pt<R, ANG, false, AR, NAP>(a, threads, grid, st);
 }
 
 }  // namespace rad

@@ -70,12 +70,14 @@ cudaError_t launch_wait_selftest(rad_ctx *ctx, double seconds) {
 
 cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st) {
   if (ang && a.recon_ang == RAD_RECON_PLM)
-    return f32 ? launch_stage_rp<float, true, true>(a, st) : launch_stage_rp<double, true, true>(a, st);
-  if (f32 && !ang && a.nap == kNapGeo4) return launch_stage_rp<float, false, false, kNapGeo4>(a, st);
+    return f32 ? launch_stage_rp<float, true, 1>(a, st) : launch_stage_rp<double, true, 1>(a, st);
+  if (ang && a.recon_ang == RAD_RECON_MAPR)
+    return f32 ? launch_stage_rp<float, true, 2>(a, st) : launch_stage_rp<double, true, 2>(a, st);
+  if (f32 && !ang && a.nap == kNapGeo4) return launch_stage_rp<float, false, 0, kNapGeo4>(a, st);
   if (f32 && ang) {
-    if (a.nap == kNapGeo4) return launch_stage_rp<float, true, false, kNapGeo4>(a, st);
-    if (a.nap == kNapGeo6) return launch_stage_rp<float, true, false, kNapGeo6>(a, st);
-    if (a.nap == kNapGeo8) return launch_stage_rp<float, true, false, kNapGeo8>(a, st);
+    if (a.nap == kNapGeo4) return launch_stage_rp<float, true, 0, kNapGeo4>(a, st);
+    if (a.nap == kNapGeo6) return launch_stage_rp<float, true, 0, kNapGeo6>(a, st);
+    if (a.nap == kNapGeo8) return launch_stage_rp<float, true, 0, kNapGeo8>(a, st);
   }
   if (f32) return ang ? launch_stage_rp<float, true>(a, st) : launch_stage_rp<float, false>(a, st);
   return ang ? launch_stage_rp<double, true>(a, st) : launch_stage_rp<double, false>(a, st);
@@ -109,8 +111,9 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
     const int threads = (a.nap / 2 + 31) / 32 * 32;
     const bool f32 = o->precision == RAD_F32;
     auto smem = [&](int kc, int depth) {
-      return f32 ? stage_smem<float, false>(threads, a.nap, kc, depth, o->tau_const > 0.0, stage_rows(o->recon))
-                 : stage_smem<double, false>(threads, a.nap, kc, depth, o->tau_const > 0.0, stage_rows(o->recon));
+      const bool mapr = o->recon_ang == RAD_RECON_MAPR;
+      return f32 ? stage_smem<float, false>(threads, a.nap, kc, depth, o->tau_const > 0.0, stage_rows(o->recon), mapr)
+                 : stage_smem<double, false>(threads, a.nap, kc, depth, o->tau_const > 0.0, stage_rows(o->recon), mapr);
     };
     const size_t budget = (size_t)200 * 1024;
     const int kmax = G.ndim >= 3 ? std::min(G.n[2], kMaxChunk) : 1;
@@ -141,6 +144,10 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
   a.edge_pq = ctx->dang.edge_pq;
   a.edge_line = ctx->dang.edge_line;
   a.line_behind = ctx->dang.line_behind;
+  a.mapr_nb = ctx->dang.mapr_nb;
+  a.mapr_minv = ctx->dang.mapr_minv;
+  a.mapr_xo = ctx->dang.mapr_xo;
+  a.mapr_xn = ctx->dang.mapr_xn;
   a.recon_ang = o->recon_ang;
   a.recon = o->recon;
   a.mode = o->coupling;
@@ -165,10 +172,11 @@ int check_stage(const StageArgs &a, bool f32, std::string &err) {
     return RAD_EUNSUPPORTED;
   }
   const int threads = (a.nap / 2 + 31) / 32 * 32;
+  const bool mapr = a.recon_ang == RAD_RECON_MAPR;
   const size_t smem = f32 ? stage_smem<float, false>(threads, a.nap, a.kc, a.depth, a.tau_const > 0.0,
-                                                     stage_rows(a.recon))
+                                                     stage_rows(a.recon), mapr)
                           : stage_smem<double, false>(threads, a.nap, a.kc, a.depth, a.tau_const > 0.0,
-                                                      stage_rows(a.recon));
+                                                      stage_rows(a.recon), mapr);
   if (smem > (size_t)227 * 1024 || threads + 32 > kStageMaxThreads) {
     err = "the stencil pipeline of this many bins does not fit one CTA in this precision";
     return RAD_EUNSUPPORTED;

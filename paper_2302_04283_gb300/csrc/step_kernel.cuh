@@ -73,6 +73,8 @@ struct StageArgs {
   const int *perm, *slot_nbr, *slot_edge, *edge_pq;
   const int *edge_line;    // latitude-longitude grids: cell behind p, cell beyond q of each side
   const int *line_behind;  // latitude-longitude grids: per bin, the sides it is the cell behind of (adjoint)
+  const int *mapr_nb;      // geodesic grids: neighbours in cyclic order, plane inverses, side midpoints
+  const double *mapr_minv, *mapr_xo, *mapr_xn;
   int recon_ang;           // RAD_RECON_DC or RAD_RECON_PLM (angular fluxes)
   int recon, mode, zero_guard;
   double n0crit, a_rad, gamma;
@@ -87,7 +89,9 @@ cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st
 // stage_<precision>_<flat|ang>.cu, one translation unit each).
 // NAP > 0 fixes the padded row length (a.nap) at compile time; 0 reads it
 // from the arguments.
-template <typename R, bool ANG, bool AP = false, int NAP = 0>
+// AR: angular reconstruction (curved space): 0 donor cell, 1 PLM along the
+// lines of a latitude-longitude grid, 2 minimum-angle planes on a geodesic grid.
+template <typename R, bool ANG, int AR = 0, int NAP = 0>
 cudaError_t launch_stage_rp(const StageArgs &a, cudaStream_t st);
 // Padded rows of the level-4, 6 and 8 geodesic grids (162, 362, 642 bins):
 // the FP32 kernels have variants with these row lengths fixed (the flat-space
@@ -449,8 +453,10 @@ __device__ __forceinline__ bool mbar_wait_parity(uint64_t *bar, uint32_t parity,
 
 // Shared-memory footprint (bytes) of k_stage.
 template <typename R, bool ANG>
-__host__ __device__ constexpr size_t stage_smem(int threads, int nap, int kc, int depth, bool tau, int rows) {
+__host__ __device__ constexpr size_t stage_smem(int threads, int nap, int kc, int depth, bool tau, int rows,
+                                                bool mapr = false) {
   return (size_t)depth * rows * nap * sizeof(R)                 // staged stencil rows
+         + (mapr ? (size_t)4 * nap * sizeof(R) : 0)             // MAPR gradients of two cells
          + (size_t)kc * nap * sizeof(R)                         // I* of the chunk
          + (size_t)kc * 5 * sizeof(R)                           // gas ux uy uz alphaE u0
          + (size_t)kc * (threads / 32) * kNRedC * sizeof(R)     // per-warp partial sums
@@ -460,8 +466,9 @@ __host__ __device__ constexpr size_t stage_smem(int threads, int nap, int kc, in
          + (size_t)2 * kMaxStages * 8 + 16;                     // full and empty mbarriers
 }
 
-template <typename R, bool ANG, int RC, bool ST2, bool TAU, bool AP = false, int NAP = 0>
-// AP: PLM angular reconstruction along the lines of a latitude-longitude grid.
+template <typename R, bool ANG, int RC, bool ST2, bool TAU, int AR = 0, int NAP = 0>
+// AR: angular reconstruction, 0 donor cell, 1 PLM along the lines of a
+// latitude-longitude grid, 2 minimum-angle planes (MAPR) on a geodesic grid.
 // NAP: the padded row length when fixed at compile time (0: a.nap).
 // Register budget: the flat FP32 DC / PLM kernels are held to 96 registers
 // (the bound of a 544-thread block) so that five 128-thread CTAs fit an SM;
@@ -473,6 +480,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   using P = P2<R>;
   using V = typename P::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool AP = AR == 1, AM = AR == 2;
   const int nap = NAP > 0 ? NAP : a.nap;                  // padded bins per row
   const int t = threadIdx.x;
   const int ncons = blockDim.x - 32;                      // consumer threads; the last warp produces
@@ -509,7 +517,8 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   R *Sc = sums + a.kc * kNRedC;                            // [kc]
   constexpr bool tau = TAU;                                // optical-depth flux weighting (Sec. 2.4)
   R *stau = Sc + a.kc;                                     // [kc][6 faces][f, u^1, u^2, u^3, u^0 of the neighbour]
-  uint64_t *bars = (uint64_t *)(((uintptr_t)(stau + (tau ? a.kc * 30 : 0)) + 15) & ~(uintptr_t)15);   // [depth] full
+  R *gbuf = stau + (tau ? a.kc * 30 : 0);                 // [2][nap][2] MAPR gradients (two cells in turn)
+  uint64_t *bars = (uint64_t *)(((uintptr_t)(gbuf + (AM ? 4 * nap : 0)) + 15) & ~(uintptr_t)15);   // [depth] full
   uint64_t *ebars = bars + kMaxStages;                                                // [depth] empty
 
   for (int c = t; c < nc; c += blockDim.x) {
@@ -642,6 +651,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   };
   // angular flux of each bin: divA = a_self I + sum_s a_nb[s] I_{m_s}
   R a_self[2] = {R(0), R(0)}, a_nb[2][kMaxSlots];
+  R xu[2][kMaxSlots][2];      // MAPR: gnomonic coordinates of each side's midpoint in its upwind cell's plane
   int nb_m[2][kMaxSlots];
   if (ANG) {
     // unrolled in FP32 so that the coefficients stay in registers; the FP64
@@ -655,6 +665,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       for (int s = 0; s < kMaxSlots; ++s) {
         a_nb[e][s] = R(0);
         nb_m[e][s] = ac ? n : 0;
+        xu[e][s][0] = xu[e][s][1] = R(0);
         int m = ac ? a.slot_nbr[6 * n + s] : -1;
         if (m < 0) continue;
         nb_m[e][s] = m;
@@ -685,6 +696,15 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
           const int l = upn ? el[isp ? 0 : 1] : el[isp ? 1 : 0];
           a_nb[e][s] = (isp ? Pv : -Pv) / dOn;
           nb_m[e][s] = m | (l << 12) | (upn ? 1 << 24 : 0);
+        } else if (AM) {
+          // as above, with the upwind cell's plane evaluated at the side's
+          // midpoint (its gnomonic coordinates in that cell's tangent plane)
+          const bool upn = isp ? sp >= R(0) : sp < R(0);
+          a_nb[e][s] = (isp ? Pv : -Pv) / dOn;
+          nb_m[e][s] = m | (upn ? 1 << 24 : 0);
+          const double *xs = (upn ? a.mapr_xo : a.mapr_xn) + 12 * n + 2 * s;
+          xu[e][s][0] = (R)xs[0];
+          xu[e][s][1] = (R)xs[1];
         } else if (isp) {
           self += PL;
           a_nb[e][s] = PR / dOn;
@@ -895,7 +915,63 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       sx = P::add(sx, divd(1, yv[1], zc, yv[2], sm, sc, sp, dlo[1], dhi[1]));
     }
     V divA = zero;
-    if (ANG) {
+    if (ANG && AM) {
+      // minimum-angle planes (MAPR): each bin's flattest plane through itself
+      // and two cyclically adjacent neighbours (gradient g = inv (dI_a, dI_b)),
+      // shared through shared memory (two cells' buffers in turn, so one
+      // barrier of the consumer warps per cell suffices), then every side's
+      // flux from its upwind cell's plane at the side's midpoint
+      const R *row = sr + H * nap;
+      R *gb = gbuf + (c & 1) * 2 * nap;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int n = b0 + e;
+        if (n < a.nang) {
+          const R In = e ? zc.y : zc.x;
+          const int *nbc = a.mapr_nb + 6 * n;
+          const double *mi = a.mapr_minv + 24 * n;
+          R dl[6];
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            const int m = nbc[q];
+            dl[q] = m >= 0 ? row[m] - In : R(0);
+          }
+          const int K = nbc[5] >= 0 ? 6 : 5;
+          R gx = R(0), gy = R(0), bq = R(0);
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            if (q < K) {
+              const int q2 = q + 1 == K ? 0 : q + 1;
+              const R x = (R)mi[4 * q] * dl[q] + (R)mi[4 * q + 1] * dl[q2];
+              const R y = (R)mi[4 * q + 2] * dl[q] + (R)mi[4 * q + 3] * dl[q2];
+              const R qq = x * x + y * y;
+              if (q == 0 || qq < bq) {
+                bq = qq;
+                gx = x;
+                gy = y;
+              }
+            }
+          }
+          gb[2 * n] = gx;
+          gb[2 * n + 1] = gy;
+        }
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(ncons) : "memory");
+      R da[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int n = b0 + e;
+        R acc = R(0);
+#pragma unroll
+        for (int s2 = 0; s2 < kMaxSlots; ++s2) {
+          const int pk = nb_m[e][s2];
+          const int u = (pk >> 24) & 1 ? n : (pk & 0xfff);
+          acc += a_nb[e][s2] * (row[u] + gb[2 * u] * xu[e][s2][0] + gb[2 * u + 1] * xu[e][s2][1]);
+        }
+        da[e] = acc;
+      }
+      divA = P::mk(da[0], da[1]);
+    } else if (ANG) {
       // the own row of this cell is slot h of the staged x1 block
       const R *row = sr + H * nap;
       R da[2];

@@ -105,7 +105,8 @@ def run_both(w, nsteps, precision="f64", recon="plm", coupling=None, dt=None, ta
     o = rad.rad_opts_default(precision=rad.RAD_F64 if precision == "f64" else rad.RAD_F32,
                              recon={"dc": rad.RAD_RECON_DC, "plm": rad.RAD_RECON_PLM, "ppm": rad.RAD_RECON_PPM}[recon],
                              coupling=cmode, tau_const=tau, rad_dom=int(rad_dom),
-                             recon_ang=rad.RAD_RECON_PLM if recon_ang == "plm" else rad.RAD_RECON_DC)
+                             recon_ang={"dc": rad.RAD_RECON_DC, "plm": rad.RAD_RECON_PLM,
+                                        "mapr": rad.RAD_RECON_MAPR}[recon_ang])
     for _ in range(nsteps):
         rad.rad_step(gc.ctx, Ig, gas_g, dt, o, src_g)
     rad.rad_check(gc.ctx)

@@ -323,11 +323,12 @@ def test_colliding_beams_cross_without_merging():
         assert got[0] > 0.05 and abs(got[0] - got[1]) <= 1e-5 * got[0]
 
 
-def _curvilinear_beam(kind, recon_ang=None, n=64):
+def _curvilinear_beam(kind, recon_ang=None, n=64, geodesic=None):
     """Energy, its centroid and the exact (semi-discrete) values for the
     curvilinear beam test in Cartesian ('mink_cart') or spherical
     ('mink_sph', spherical tetrad: 1hat = phi, 2hat = r, 3hat = theta)
-    coordinates."""
+    coordinates, on a 16 x 32 latitude-longitude grid or (geodesic = level)
+    a geodesic one."""
     t_end, rate, half = math.sqrt(2.0), 10.0, math.pi / 8
     x0, beam = np.array([1.5, -0.5, 0.0]), np.array([1.0, 1.0, 0.0]) / math.sqrt(2.0)
     if kind == "mink_cart":
@@ -355,7 +356,7 @@ def _curvilinear_beam(kind, recon_ang=None, n=64):
             return np.stack([ep, er, et], -2)
     ctx = rad.rad_create(torch.cuda.current_stream())
     try:
-        na, nap = rad.rad_init_angles_latlong(ctx, 16, 32)
+        na, nap = rad.rad_init_angles(ctx, geodesic) if geodesic else rad.rad_init_angles_latlong(ctx, 16, 32)
         rad.rad_set_metric(ctx, kind, 0.0, 3, xf, (("outflow", "outflow"),) * 3)
         d, dO, _ = rad.rad_get_angles(ctx, na)
         dt = rad.rad_cfl_dt(ctx, 0.3)
@@ -384,6 +385,21 @@ def _curvilinear_beam(kind, recon_ang=None, n=64):
         rad.rad_destroy(ctx)
     cen = (E[..., None] * pos).sum((0, 1, 2)) / E.sum()
     return E.sum(), E_exact, float(np.linalg.norm(cen - cen_exact))
+
+
+def test_mapr_beam_is_less_diffusive_than_donor_cell():
+    """Sec. 3: the paper shows minimum-angle plane reconstruction reducing
+    the angular diffusion of a beam whose angular fluxes come from the
+    coordinates (its snake-coordinate test); here the curvilinear beam in
+    spherical coordinates on a level-7 geodesic grid (492 bins): energy
+    conserved to 1e-5 either way, and the centroid closer to the exact value
+    with MAPR than with donor-cell angular fluxes."""
+    Ed, Ede, dd = _curvilinear_beam("mink_sph", rad.RAD_RECON_DC, geodesic=7)
+    Em, Eme, dm = _curvilinear_beam("mink_sph", rad.RAD_RECON_MAPR, geodesic=7)
+    print(f"geodesic beam: centroid offsets {dd:.4f} (DC) {dm:.4f} (MAPR)")
+    for E, Ee in ((Ed, Ede), (Em, Eme)):
+        assert abs(E / Ee - 1.0) < 1e-5
+    assert dm < dd
 
 
 def test_curvilinear_beam_is_the_same_in_cartesian_and_spherical_coordinates():
