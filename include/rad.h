@@ -187,7 +187,7 @@ typedef struct {
                         adjacent neighbours in its gnomonic tangent plane,
                         evaluated at the side midpoints; RAD_EUNSUPPORTED on
                         a latitude-longitude grid).  rad_step_adjoint takes
-                        DC or PLM. */
+                        all three. */
 } rad_opts;
 
 /* Fill *opts with the defaults above (FP64, PLM, thermal coupling). */
@@ -291,9 +291,9 @@ int rad_step_host(rad_ctx *ctx, int n_items, const rad_host_item *items, double 
  * is frozen and lamT_n = lamT_np1.  With opts->tau_const > 0 (the
  * optical-depth weighting of Sec. 2.4) the opacity gradients include the
  * path through the face weights.  Any spatial reconstruction (DC, PLM, PPM)
- * and either angular one (DC, or PLM along the lines of a latitude-longitude
- * grid), the limiters differentiated on their active branches; rad_dom must
- * be 0 (RAD_EUNSUPPORTED otherwise).  lam arrays use the intensity
+ * and any angular one (DC, line PLM, MAPR), the limiters and the plane choice
+ * differentiated on their active branches; rad_dom must be 0
+ * (RAD_EUNSUPPORTED otherwise).  lam arrays use the intensity
  * layout and precision; lamT arrays are device FP64 [k][j][i].  lamT_np1 may
  * be NULL (zero), lamT_n may be NULL (not written) and may equal lamT_np1;
  * g_eta may be NULL.

@@ -279,7 +279,8 @@ namespace {
 
 template <typename R>
 cudaError_t launch_transport_adj_any(const AdjArgs &A, bool ang, cudaStream_t st) {
-  if (ang && A.s.recon_ang == RAD_RECON_PLM) return launch_transport_adj<R, true, true>(A, st);
+  if (ang && A.s.recon_ang == RAD_RECON_PLM) return launch_transport_adj<R, true, 1>(A, st);
+  if (ang && A.s.recon_ang == RAD_RECON_MAPR) return launch_transport_adj<R, true, 2>(A, st);
   return ang ? launch_transport_adj<R, true>(A, st) : launch_transport_adj<R, false>(A, st);
 }
 

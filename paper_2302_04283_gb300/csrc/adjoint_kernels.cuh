@@ -182,9 +182,9 @@ __device__ __forceinline__ void edge_grad(bool plm, bool right, const R *w, R &p
 // Transposed transport of one stage (gather form, one thread per target bin).
 // PPM: the spatial reconstruction is PPM (each face state depends on the five
 // cells around its upwind cell) instead of DC / PLM (three cells).
-// AP (with ANG): PLM angular reconstruction along the lines of a
-// latitude-longitude grid instead of donor-cell angular fluxes.
-template <typename R, bool ANG, int MAXT, bool TAU, bool PPM, bool AP>
+// AR (with ANG): angular reconstruction, 0 donor cell, 1 PLM along the lines
+// of a latitude-longitude grid, 2 minimum-angle planes on a geodesic grid.
+template <typename R, bool ANG, int MAXT, bool TAU, bool PPM, int AR>
 __global__ void __launch_bounds__(MAXT, sizeof(R) == 8 ? 1 : 1280 / MAXT) k_transport_adj(AdjArgs A) {
   using Col = typename GeoTypes<R>::Col;
   using Face = typename GeoTypes<R>::Face;
@@ -192,6 +192,7 @@ __global__ void __launch_bounds__(MAXT, sizeof(R) == 8 ? 1 : 1280 / MAXT) k_tran
   // cr + 1 for cr = -HW .. HW - 1 (NF faces); 1/dV and mu at -HW .. HW (NM);
   // the stencils of those faces span -(HW + SW) .. HW + SW (NV values)
   constexpr int SW = PPM ? 2 : 1, HW = SW + 1, NF = 2 * HW, NM = 2 * HW + 1, NV = 2 * (HW + SW) + 1;
+  constexpr bool AP = AR == 1, AM = AR == 2;
   const StageArgs &a = A.s;
   const int n = threadIdx.x;
   const bool act = n < a.nang;
@@ -271,8 +272,7 @@ __global__ void __launch_bounds__(MAXT, sizeof(R) == 8 ? 1 : 1280 / MAXT) k_tran
   constexpr int NE = AP ? kMaxSlots + kMaxBehind : 1;
   R ap_P[NE];
   int ap_e[NE], ap_p[NE], ap_q[NE], ap_u[NE], ap_d[NE], ap_b[NE];
-  if (AP) {
-    auto edge_P = [&](int e, bool &upp) -> R {
+  auto edge_P = [&](int e, bool &upp) -> R {
       const double *eg = a.edge_geo + 8 * e;
       const R x = (R)eg[0], yv = (R)eg[1], z = (R)eg[2], len = (R)eg[6];
       const R pr[10] = {R(1), x, yv, z, x * x, x * yv, x * z, yv * yv, yv * z, z * z};
@@ -285,7 +285,19 @@ __global__ void __launch_bounds__(MAXT, sizeof(R) == 8 ? 1 : 1280 / MAXT) k_tran
       const R sp = -((R)eg[3] * q0 + (R)eg[4] * q1 + (R)eg[5] * q2);
       upp = sp >= R(0);                       // upwind: p (ties to p, as the forward)
       return len * sp * (cg.M[0][0] + cg.M[0][1] * x + cg.M[0][2] * yv + cg.M[0][3] * z);
-    };
+  };
+  // MAPR (AM): every side's prefactor and upwind side for this column
+  __shared__ R amP[AM ? 3 * kMaxBinsStep : 1];
+  __shared__ unsigned char amUp[AM ? 3 * kMaxBinsStep : 1];
+  if (AM) {
+    for (int e = threadIdx.x; e < a.n_edge; e += blockDim.x) {
+      bool upp;
+      amP[e] = edge_P(e, upp);
+      amUp[e] = upp;
+    }
+    __syncthreads();
+  }
+  if (AP) {
     for (int s = 0; s < NE; ++s) {
       ap_P[s] = R(0);
       ap_e[s] = -1;
@@ -322,7 +334,7 @@ __global__ void __launch_bounds__(MAXT, sizeof(R) == 8 ? 1 : 1280 / MAXT) k_tran
   // angular: transposed coefficients
   R at_self = R(0), at_nb[kMaxSlots];
   int nb_m[kMaxSlots];
-  if (ANG && !AP) {
+  if (ANG && !AP && !AM) {
     R self = R(0);
     for (int s = 0; s < kMaxSlots; ++s) {
       at_nb[s] = R(0);
@@ -527,7 +539,7 @@ __global__ void __launch_bounds__(MAXT, sizeof(R) == 8 ? 1 : 1280 / MAXT) k_tran
         }
       }
     }
-    if (ANG && !AP) {
+    if (ANG && !AP && !AM) {
       R ga = at_self * mu0;
       for (int s = 0; s < kMaxSlots; ++s) ga += at_nb[s] * mu[addr(i, j, k, nb_m[s])];
       lam -= ga;
@@ -543,6 +555,50 @@ __global__ void __launch_bounds__(MAXT, sizeof(R) == 8 ? 1 : 1280 / MAXT) k_tran
         R d[3];
         dphi(true, false, Il[addr(i, j, k, ap_b[s])], Il[addr(i, j, k, ap_u[s])], Il[addr(i, j, k, ap_d[s])], d);
         lam += lphiA * ((ap_b[s] == n ? d[0] : R(0)) + (ap_u[s] == n ? d[1] : R(0)) + (ap_d[s] == n ? d[2] : R(0)));
+      }
+    }
+    if (AM && act) {
+      // a side's upwind value is I_u + g_u . x = I_u + w_a (I_a - I_u) +
+      // w_b (I_b - I_u), (w_a, w_b) = A^T x with A the inverse of u's chosen
+      // plane (cells a, b) on its active branch; this bin enters the sides
+      // of u = itself or a neighbour whose chosen plane holds it
+#pragma unroll 1
+      for (int ci = 0; ci <= kMaxSlots; ++ci) {
+        const int u = ci == 0 ? n : a.slot_nbr[6 * n + ci - 1];
+        if (u < 0) continue;
+        const int *nbc = a.mapr_nb + 6 * u;
+        const double *mi = a.mapr_minv + 24 * u;
+        const R Iu = Il[addr(i, j, k, u)];
+        R dl[6];
+        for (int q = 0; q < 6; ++q) dl[q] = nbc[q] >= 0 ? Il[addr(i, j, k, nbc[q])] - Iu : R(0);
+        const int K = nbc[5] >= 0 ? 6 : 5;
+        int best = 0;
+        R bq = R(0);
+        for (int q = 0; q < K; ++q) {
+          const int q2 = q + 1 == K ? 0 : q + 1;
+          const R x = (R)mi[4 * q] * dl[q] + (R)mi[4 * q + 1] * dl[q2];
+          const R y = (R)mi[4 * q + 2] * dl[q] + (R)mi[4 * q + 3] * dl[q2];
+          const R qq = x * x + y * y;
+          if (q == 0 || qq < bq) {
+            bq = qq;
+            best = q;
+          }
+        }
+        const int b2 = best + 1 == K ? 0 : best + 1;
+        const int ma = nbc[best], mb = nbc[b2];
+        if (n != u && n != ma && n != mb) continue;
+        const double *m4 = mi + 4 * best;
+#pragma unroll 1
+        for (int s = 0; s < kMaxSlots; ++s) {
+          if (a.slot_nbr[6 * u + s] < 0) continue;
+          const int e = a.slot_edge[6 * u + s];
+          const int p = a.edge_pq[2 * e], q = a.edge_pq[2 * e + 1];
+          if ((u == p) != (amUp[e] != 0)) continue;          // u is not upwind of this side
+          const double *xs = a.mapr_xo + 12 * u + 2 * s;
+          const R wa = (R)(m4[0] * xs[0] + m4[2] * xs[1]), wb = (R)(m4[1] * xs[0] + m4[3] * xs[1]);
+          const R dv = (n == u ? R(1) - wa - wb : R(0)) + (n == ma ? wa : R(0)) + (n == mb ? wb : R(0));
+          lam += -amP[e] * (mu[addr(i, j, k, p)] / (R)a.dOmega[p] - mu[addr(i, j, k, q)] / (R)a.dOmega[q]) * dv;
+        }
       }
     }
     if (tauw) {
@@ -594,26 +650,26 @@ __global__ void k_tau_grad(const double *gtau, int n1, int n2, int n3, int ndim,
 
 }  // namespace
 
-template <typename R, bool ANG, bool AP, int MAXT>
+template <typename R, bool ANG, int AR, int MAXT>
 void launch_tadj(const AdjArgs &A, bool tau, bool ppm, dim3 grid, int threads, cudaStream_t st) {
   if (ppm)
-    tau ? k_transport_adj<R, ANG, MAXT, true, true, AP><<<grid, threads, 0, st>>>(A)
-        : k_transport_adj<R, ANG, MAXT, false, true, AP><<<grid, threads, 0, st>>>(A);
+    tau ? k_transport_adj<R, ANG, MAXT, true, true, AR><<<grid, threads, 0, st>>>(A)
+        : k_transport_adj<R, ANG, MAXT, false, true, AR><<<grid, threads, 0, st>>>(A);
   else
-    tau ? k_transport_adj<R, ANG, MAXT, true, false, AP><<<grid, threads, 0, st>>>(A)
-        : k_transport_adj<R, ANG, MAXT, false, false, AP><<<grid, threads, 0, st>>>(A);
+    tau ? k_transport_adj<R, ANG, MAXT, true, false, AR><<<grid, threads, 0, st>>>(A)
+        : k_transport_adj<R, ANG, MAXT, false, false, AR><<<grid, threads, 0, st>>>(A);
 }
 
-// AP: angular PLM on a latitude-longitude grid (curved space only)
-template <typename R, bool ANG, bool AP = false>
+// AR: angular reconstruction (curved space only): 0 donor cell, 1 line PLM, 2 MAPR
+template <typename R, bool ANG, int AR = 0>
 cudaError_t launch_transport_adj(const AdjArgs &A, cudaStream_t st) {
   int threads = (A.s.nap + 31) / 32 * 32;
   int nchunk = (A.s.n3 + A.s.kc - 1) / A.s.kc;
   dim3 grid((unsigned)((long long)A.s.n1 * A.s.n2 * nchunk));
   const bool tau = A.s.tau_const > 0.0, ppm = A.s.recon == RAD_RECON_PPM;
-  if (threads <= 256) launch_tadj<R, ANG, AP, 256>(A, tau, ppm, grid, threads, st);
-  else if (threads <= 512) launch_tadj<R, ANG, AP, 512>(A, tau, ppm, grid, threads, st);
-  else launch_tadj<R, ANG, AP, 1024>(A, tau, ppm, grid, threads, st);
+  if (threads <= 256) launch_tadj<R, ANG, AR, 256>(A, tau, ppm, grid, threads, st);
+  else if (threads <= 512) launch_tadj<R, ANG, AR, 512>(A, tau, ppm, grid, threads, st);
+  else launch_tadj<R, ANG, AR, 1024>(A, tau, ppm, grid, threads, st);
   if (tau) {
     const StageArgs &a = A.s;
     const long long ncell = (long long)a.n1 * a.n2 * a.n3;
@@ -624,12 +680,14 @@ cudaError_t launch_transport_adj(const AdjArgs &A, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Explicitly instantiated in adjoint_tadj_<precision>_<flat|ang|angplm>.cu.
+// Explicitly instantiated in adjoint_tadj_<precision>_<flat|ang|angplm|angmapr>.cu.
 extern template cudaError_t launch_transport_adj<float, false>(const AdjArgs &, cudaStream_t);
 extern template cudaError_t launch_transport_adj<float, true>(const AdjArgs &, cudaStream_t);
 extern template cudaError_t launch_transport_adj<double, false>(const AdjArgs &, cudaStream_t);
 extern template cudaError_t launch_transport_adj<double, true>(const AdjArgs &, cudaStream_t);
-extern template cudaError_t launch_transport_adj<float, true, true>(const AdjArgs &, cudaStream_t);
-extern template cudaError_t launch_transport_adj<double, true, true>(const AdjArgs &, cudaStream_t);
+extern template cudaError_t launch_transport_adj<float, true, 1>(const AdjArgs &, cudaStream_t);
+extern template cudaError_t launch_transport_adj<double, true, 1>(const AdjArgs &, cudaStream_t);
+extern template cudaError_t launch_transport_adj<float, true, 2>(const AdjArgs &, cudaStream_t);
+extern template cudaError_t launch_transport_adj<double, true, 2>(const AdjArgs &, cudaStream_t);
 
 }  // namespace rad

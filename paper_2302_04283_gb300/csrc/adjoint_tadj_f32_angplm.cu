@@ -4,6 +4,6 @@
 
 namespace rad {
 
-template cudaError_t launch_transport_adj<float, true, true>(const AdjArgs &A, cudaStream_t st);
+template cudaError_t launch_transport_adj<float, true, 1>(const AdjArgs &A, cudaStream_t st);
 
 }  // namespace rad

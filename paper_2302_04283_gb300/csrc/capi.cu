@@ -369,8 +369,6 @@ int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double d
   if ((st = check_gas(ctx, gas, o, true)) != RAD_OK) return st;
   if (o->rad_dom)
     return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers the coupling at the gas velocity (rad_dom = 0)");
-  if (o->recon_ang == RAD_RECON_MAPR)
-    return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers donor-cell and line-PLM angular fluxes");
   if (!I_n || !lam_np1 || !lam_n || !g_aa || !g_as) return fail(ctx, RAD_EINVAL, "null argument");
   if (!(dt > 0.0)) return fail(ctx, RAD_EINVAL, "dt must be > 0");
   if (ctx->ang.n_ang > rad::kMaxBinsStep)

@@ -144,6 +144,7 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
   a.edge_pq = ctx->dang.edge_pq;
   a.edge_line = ctx->dang.edge_line;
   a.line_behind = ctx->dang.line_behind;
+  a.n_edge = ctx->ang.n_edge;
   a.mapr_nb = ctx->dang.mapr_nb;
   a.mapr_minv = ctx->dang.mapr_minv;
   a.mapr_xo = ctx->dang.mapr_xo;

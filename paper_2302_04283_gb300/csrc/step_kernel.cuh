@@ -73,6 +73,7 @@ struct StageArgs {
   const int *perm, *slot_nbr, *slot_edge, *edge_pq;
   const int *edge_line;    // latitude-longitude grids: cell behind p, cell beyond q of each side
   const int *line_behind;  // latitude-longitude grids: per bin, the sides it is the cell behind of (adjoint)
+  int n_edge;              // sides of the angle grid
   const int *mapr_nb;      // geodesic grids: neighbours in cyclic order, plane inverses, side midpoints
   const double *mapr_minv, *mapr_xo, *mapr_xn;
   int recon_ang;           // RAD_RECON_DC or RAD_RECON_PLM (angular fluxes)

@@ -1,14 +1,18 @@
 """Minimum-angle plane reconstruction (MAPR) of the angular face values on
 geodesic grids (recon_ang = RAD_RECON_MAPR) through the C ABI, against the
 oracle: FP64 1e-12, FP32 2e-5 relative (normwise per output), as for every
-step; and the options that refuse it."""
+step; the adjoint with it against the oracle's reverse mode (FP64 1e-11,
+FP32 2e-4); and the options that refuse it."""
 import numpy as np
 import pytest
 import torch
 
 import paper_2302_04283_gb300 as rad
 import workloads as W
-from tests.harness import GpuCase, rel_err, run_both
+from oracle import adjoint as OA
+from oracle import cfl as OCFL
+from oracle import step as OS
+from tests.harness import GpuCase, match_bins, oracle_gas, oracle_setup, rel_err, run_both
 
 pytestmark = pytest.mark.gpu
 
@@ -66,13 +70,72 @@ def test_mapr_arguments_are_checked():
     try:
         I = torch.zeros((2, 4, 4, gc.n_ap), dtype=torch.float64, device="cuda")
         z = torch.zeros((2, 4, 4), dtype=torch.float64, device="cuda")
-        with pytest.raises(rad.RadError) as e:           # the adjoint does not cover it
-            rad.rad_step_adjoint(gc.ctx, I, gc.gas(w), 0.01,
-                                 rad.rad_opts_default(coupling=rad.RAD_COUPLE_NONE, recon_ang=rad.RAD_RECON_MAPR),
-                                 I, torch.zeros_like(I), None, None, z, z.clone())
-        assert e.value.status == rad.RAD_EUNSUPPORTED
         with pytest.raises(rad.RadError) as e:           # as a spatial reconstruction it is unknown
             rad.rad_step(gc.ctx, I, gc.gas(w), 0.01, rad.rad_opts_default(recon=rad.RAD_RECON_MAPR))
         assert e.value.status == rad.RAD_EINVAL
     finally:
         gc.close()
+
+
+MAPR_ADJ_CASES = [
+    # name, sizes, level, spatial recon, coupling, C, precision
+    ("torus3d", (6, 6, 4), 2, "plm", "emissivity", 0.0, "f64"),
+    ("torus3d_big", (5, 4, 4), 1, "plm", "thermal", 0.0, "f64"),      # pentagons, moving gas, scattering
+    ("adjoint2d", (10, 8, 1), 2, "ppm", "emissivity", 5.0, "f64"),    # 2D, PPM, optical-depth weighting
+    ("torus3d", (6, 6, 4), 2, "plm", "emissivity", 0.0, "f32"),
+]
+
+
+@pytest.mark.parametrize("name,n,level,recon,coupling,C,prec", MAPR_ADJ_CASES)
+def test_mapr_adjoint_matches_oracle(name, n, level, recon, coupling, C, prec):
+    w = W.make(name, n=n, level=level)
+    rng = np.random.default_rng(23)
+    if coupling == "emissivity":
+        if w["eta"] is None:
+            w["eta"] = 10.0 ** rng.uniform(-1, 1, w["T"].shape) / (4 * np.pi)
+    else:
+        w["eta"] = None
+    w["mode"] = coupling
+    if C > 0 and not np.any(w["u"]):
+        v = rng.uniform(-1, 1, w["u"].shape)
+        v *= 0.3 / np.sqrt((v * v).sum(-1)).max()
+        w["u"] = v / np.sqrt(1 - (v * v).sum(-1))[..., None]
+    st = oracle_setup(w)
+    gc = GpuCase(w)
+    try:
+        gmap = match_bins(gc.dir, st.ang.dir.numpy())
+        dt = OCFL.cfl_dt(st, w["cfl"])
+        lam = rng.normal(size=w["I0"].shape)
+        lamT = rng.normal(size=w["T"].shape) if coupling == "thermal" else None
+        I0, T0 = torch.tensor(w["I0"]), torch.tensor(w["T"])
+        lam_o, lamT_o, ga_o, gs_o, ge_o = OA.step_vjp(
+            I0, T0, oracle_gas(w), dt, st, OS.Opts(recon=recon, mode=coupling, tau_const=C, recon_ang="mapr"),
+            torch.tensor(lam), None if lamT is None else torch.tensor(lamT))
+        f64 = prec == "f64"
+        tdt = torch.float64 if f64 else torch.float32
+        o = rad.rad_opts_default(precision=rad.RAD_F64 if f64 else rad.RAD_F32,
+                                 coupling=rad.RAD_COUPLE_THERMAL if coupling == "thermal" else rad.RAD_COUPLE_EMISSIVITY,
+                                 recon={"dc": rad.RAD_RECON_DC, "plm": rad.RAD_RECON_PLM, "ppm": rad.RAD_RECON_PPM}[recon],
+                                 tau_const=C, recon_ang=rad.RAD_RECON_MAPR)
+        Ig = gc.to_gpu_I(w["I0"], gmap, tdt)
+        lg = gc.to_gpu_I(lam, gmap, tdt)
+        ln = torch.zeros_like(Ig)
+        gas = gc.gas(w)
+        lTg = None if lamT is None else torch.tensor(lamT, device="cuda")
+        lTn = None if lamT is None else torch.zeros_like(lTg)
+        ga, gs = torch.zeros_like(gas["rho"]), torch.zeros_like(gas["rho"])
+        ge = torch.zeros_like(ga) if coupling == "emissivity" else None
+        rad.rad_step_adjoint(gc.ctx, Ig, gas, dt, o, lg, ln, lTg, lTn, ga, gs, ge)
+        torch.cuda.synchronize()
+        rad.rad_check(gc.ctx)
+        tol = 1e-11 if f64 else 2e-4
+        assert rel_err(gc.from_gpu_I(ln.double(), gmap), lam_o.numpy()) < tol
+        assert rel_err(ga.cpu().numpy(), ga_o.numpy()) < tol
+        assert rel_err(gs.cpu().numpy(), gs_o.numpy()) < (2e-10 if f64 and coupling == "thermal" else tol)
+        if ge is not None:
+            assert rel_err(ge.cpu().numpy(), ge_o.numpy()) < tol
+        if lTn is not None:
+            assert rel_err(lTn.cpu().numpy(), lamT_o.numpy()) < tol
+    finally:
+        gc.close()
+

@@ -103,3 +103,51 @@ def test_mapr_is_refused_on_latlong_grids():
     ang = LatLongGrid(3, 6)
     with pytest.raises(ValueError):
         TR.angular_face_values(torch.ones(ang.n_ang, dtype=torch.float64), ang, "mapr")
+
+
+def test_mapr_gradient_matches_central_differences():
+    """Away from ties the chosen plane is locally fixed, so the step is
+    differentiable: reverse-mode AD of the oracle against central differences
+    of its forward (2D Kerr-Schild, level-2 geodesic grid, two steps) in
+    alpha_a and in intensities."""
+    import workloads as W
+    from oracle import adjoint as A
+    from oracle import cfl as CF
+    w = W.make("adjoint2d", n=(6, 4, 1), level=2)
+    ang = GeodesicGrid(2)
+    st = Setup(Grid(w["kind"], w["spin"], w["xf"], w["bc"], w["ndim"]), ang)
+    gas = {k: (torch.tensor(w[k]) if w[k] is not None else None)
+           for k in ("rho", "u", "alpha_a", "alpha_s", "eta")}
+    dt = CF.cfl_dt(st, 0.3)
+    opts = S.Opts(mode="emissivity", recon_ang="mapr")
+    I0, T0 = torch.tensor(w["I0"]), torch.tensor(w["T"])
+    nsteps = 2
+    _, grads = A.gradient(I0, T0, gas, dt, st, opts, nsteps)
+    I0r = I0.clone().requires_grad_(True)
+    I, T = I0r, T0
+    for _ in range(nsteps):
+        I, T, _, _ = S.rk2_step(I, T, gas, dt, st, opts)
+    gI = torch.autograd.grad(A.loss_outer(I, st), I0r)[0]
+
+    def loss_with(field, idx, h):
+        g2 = {k: (x.clone() if x is not None else None) for k, x in gas.items()}
+        Iv = I0.clone()
+        if field == "I":
+            Iv[idx] += h
+        else:
+            g2[field][idx] += h
+        Iv2, T2 = Iv, T0
+        for _ in range(nsteps):
+            Iv2, T2, _, _ = S.rk2_step(Iv2, T2, g2, dt, st, opts)
+        return float(A.loss_outer(Iv2, st))
+
+    checks = [("alpha_a", grads[0], gas["alpha_a"], (0, 1, 5)), ("alpha_a", grads[0], gas["alpha_a"], (0, 3, 4))]
+    for idx in [(0, 1, 5, 3), (0, 2, 5, 17), (0, 3, 4, 30)]:
+        checks.append(("I", gI, I0, idx))
+    for field, grad, base, idx in checks:
+        gmax = float(grad.abs().max())
+        h = 1e-6 * max(abs(float(base[idx])), 1e-3 * float(base.abs().max()))
+        fd = (loss_with(field, idx, h) - loss_with(field, idx, -h)) / (2 * h)
+        ad = float(grad[idx])
+        assert abs(fd - ad) <= 1e-6 * max(abs(ad), 2e-2 * gmax), (field, idx, fd, ad)
+
