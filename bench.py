@@ -468,8 +468,22 @@ def run_e2e(args, rad, ctx, dt, opts, prec, mom, sh, na, nap, tdt, dev, world):
     h2d = hI.numel() * hI.element_size() + sum(v.numel() * v.element_size() for v in hgas.values()) + \
         hT.numel() * hT.element_size()
     d2h = hR.numel() * hR.element_size() + hT.numel() * hT.element_size()
+    # this machine's pinned host-to-device rate (one copy of the intensity
+    # array, after the timed region): the step rate the uploads alone allow
+    dI = torch.empty_like(hI, device=dev)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dI.copy_(hI, non_blocking=True)
+    e0.record(s)
+    dI.copy_(hI, non_blocking=True)
+    e1.record(s)
+    torch.cuda.synchronize()
+    h2d_gbs = hI.numel() * hI.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del dI
     return {"value": rate, "unit": "cell-angle updates/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "h2d_gbs_measured": round(h2d_gbs, 1),
+            "upload_bound_value": sh[0] * sh[1] * sh[2] * na / (h2d / (h2d_gbs * 1e9)),
             "api": "rad_step_host (host buffers; uploads, read-backs and moments on their own streams, overlapping the steps)"}
 
 

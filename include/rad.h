@@ -56,7 +56,7 @@ typedef enum {
   RAD_ENOCONV = -4,       /* quartic without a bracketed root / Newton cap hit */
   RAD_ENONFINITE = -5,    /* a non-finite intensity or temperature was produced */
   RAD_ESTATE = -6,        /* call out of order (e.g. step before set_metric) */
-  RAD_EUNSUPPORTED = -7   /* valid request this build does not implement */
+  RAD_EUNSUPPORTED = -7   /* a valid request the library does not implement */
 } rad_status;
 
 enum { RAD_MINK_CART = 0, RAD_MINK_SPH = 1, RAD_KS_SPH = 2 };
