@@ -220,8 +220,9 @@ int rad_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt,
  * is a service of this library).  For callers that may not allocate device
  * memory once running: a host framework that owns all device memory through
  * its own pool, or a loop that cannot take the implicit synchronisation of
- * cudaMalloc / cudaFree.  Same arguments, arithmetic and results as
- * rad_step, but the stage scratch (one intensity array and one temperature
+ * cudaMalloc / cudaFree.  Same arguments, options (every recon, recon_ang,
+ * tau_const, rad_dom and coupling that rad_step takes), host-side checks,
+ * kernels and results (bit for bit) as rad_step, but the stage scratch (one intensity array and one temperature
  * array) lives in a 32 MiB static device array that every GPU loading this
  * library holds until the process exits.  Grids needing more
  * (n_cells * n_ang_padded * element size, rounded up to 256 bytes, plus

@@ -305,7 +305,12 @@ static int check_opts(rad_ctx *ctx, const rad_opts *o) {
   return RAD_OK;
 }
 
-int rad_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src) {
+}  // extern "C"
+
+// The host-side checks every RK2 step entry (rad_step, rad_step_noalloc)
+// makes before anything is launched: options, gas fields, the intensity
+// pointer, dt, the bin count and the 32-bit element index.
+int rad::check_step_args(rad_ctx *ctx, const void *I, const rad_gas *gas, double dt, const rad_opts *o) {
   if (!ctx) return RAD_EINVAL;
   if (!ctx->have_metric) return fail(ctx, RAD_ESTATE, "rad_set_metric has not been called");
   int st = check_opts(ctx, o);
@@ -314,12 +319,22 @@ int rad_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opt
   if (!I || !aligned16(I)) return fail(ctx, RAD_EINVAL, "I must be a 16-byte aligned device pointer");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, RAD_EINVAL, "dt must be finite and > 0");
   if (ctx->ang.n_ang > rad::kMaxBinsStep)
-    return fail(ctx, RAD_EUNSUPPORTED, "rad_step supports up to 812 bins (geodesic level 9)");
+    return fail(ctx, RAD_EUNSUPPORTED, "the step supports up to 812 bins (geodesic level 9)");
+  const rad::DevGeom &G = ctx->geom;
+  const size_t ncell = (size_t)G.n[0] * G.n[1] * G.n[2];
+  if (ncell * ctx->ang.n_ap >= ((size_t)1 << 32))
+    return fail(ctx, RAD_EUNSUPPORTED, "the step handles fewer than 2^32 intensity elements in one block");
+  return RAD_OK;
+}
+
+extern "C" {
+
+int rad_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src) {
+  int st = rad::check_step_args(ctx, I, gas, dt, o);
+  if (st != RAD_OK) return st;
   const rad::DevGeom &G = ctx->geom;
   size_t ncell = (size_t)G.n[0] * G.n[1] * G.n[2];
   size_t esz = o->precision == RAD_F32 ? 4 : 8;
-  if (ncell * ctx->ang.n_ap >= ((size_t)1 << 32))
-    return fail(ctx, RAD_EUNSUPPORTED, "rad_step: more than 2^32 intensity elements in one block");
   size_t need = ncell * ctx->ang.n_ap * esz;
   if (ctx->scratch_I_bytes < need) {
     cudaStreamSynchronize(ctx->stream);

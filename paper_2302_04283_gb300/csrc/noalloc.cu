@@ -67,23 +67,9 @@ int fail(rad_ctx *ctx, int code, const std::string &msg) {
 
 extern "C" int rad_step_noalloc(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opts *o,
                                 double *gas_src) {
-  if (!ctx) return RAD_EINVAL;
-  if (!ctx->have_metric) return fail(ctx, RAD_ESTATE, "rad_set_metric has not been called");
-  if (!o || !gas) return fail(ctx, RAD_EINVAL, "null opts or gas");
-  if (o->precision != RAD_F64 && o->precision != RAD_F32) return fail(ctx, RAD_EINVAL, "bad precision");
-  if (o->recon != RAD_RECON_DC && o->recon != RAD_RECON_PLM) return fail(ctx, RAD_EINVAL, "bad recon");
-  if (o->coupling < RAD_COUPLE_THERMAL || o->coupling > RAD_COUPLE_NONE) return fail(ctx, RAD_EINVAL, "bad coupling");
-  if (o->coupling == RAD_COUPLE_THERMAL && !(o->gamma > 1.0)) return fail(ctx, RAD_EINVAL, "gamma must be > 1");
-  if (!(o->n0crit >= 0.0)) return fail(ctx, RAD_EINVAL, "n0crit must be >= 0");
-  if (o->coupling != RAD_COUPLE_NONE && (!gas->rho || !gas->u || !gas->alpha_a || !gas->alpha_s))
-    return fail(ctx, RAD_EINVAL, "gas fields rho, u, alpha_a, alpha_s are required for coupling");
-  if (o->coupling == RAD_COUPLE_EMISSIVITY && !gas->eta)
-    return fail(ctx, RAD_EINVAL, "emissivity coupling needs gas->eta");
-  if (!gas->T) return fail(ctx, RAD_EINVAL, "gas->T is required");
-  if (!I || ((uintptr_t)I & 15u)) return fail(ctx, RAD_EINVAL, "I must be a 16-byte aligned device pointer");
-  if (!(dt > 0.0) || !(dt < 1e300)) return fail(ctx, RAD_EINVAL, "dt must be finite and > 0");
-  if (ctx->ang.n_ang > rad::kMaxBinsStep)
-    return fail(ctx, RAD_EUNSUPPORTED, "rad_step_noalloc supports up to 812 bins (geodesic level 9)");
+  // the same host-side checks as rad_step, before anything is launched
+  const int chk = rad::check_step_args(ctx, I, gas, dt, o);
+  if (chk != RAD_OK) return chk;
   const rad::DevGeom &G = ctx->geom;
   const size_t ncell = (size_t)G.n[0] * G.n[1] * G.n[2];
   const size_t esz = o->precision == RAD_F32 ? 4 : 8;

@@ -148,6 +148,9 @@ struct rad_ctx {
 
 namespace rad {
 
+// capi.cu: the checks shared by every RK2 step entry point (sets ctx->last_error)
+int check_step_args(rad_ctx *ctx, const void *I, const rad_gas *gas, double dt, const rad_opts *o);
+
 // geom.cu
 int compute_geometry(rad_ctx *ctx, std::string &err);
 void free_geometry(DevGeom &g);
