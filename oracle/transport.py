@@ -262,11 +262,13 @@ def face_states(Ie, grid, d, recon):
     return IL + 0.5 * sL, IR - 0.5 * sR
 
 
-def _gas_ghosts(field, grid):
+def _gas_ghosts(field, grid, vector=False):
     """Gas field [n3, n2, n1, ...] extended by one ghost layer per side in every
-    flux dimension: periodic wrap, outflow copy, polar mirror (the mirrored
-    cell across the pole; polar faces have zero area, so its value never
-    reaches a flux)."""
+    flux dimension: periodic wrap, outflow copy, polar mirror (the cell across
+    the pole, at phi + pi; a tetrad-frame vector field [..., 3] (vector=True)
+    is rotated like the angle bins, by pi about 2hat, so u^1hat and u^3hat
+    change sign).  Polar faces have zero area, so a polar ghost's value never
+    reaches a flux."""
     N1, N2, N3 = grid.n
     ext = field
     for d in range(grid.ndim):
@@ -282,6 +284,8 @@ def _gas_ghosts(field, grid):
             v = ext.narrow(ax, src, 1)
             if kind == "polar":
                 v = torch.roll(v, shifts=-(N3 // 2), dims=0)
+                if vector:
+                    v = v * torch.tensor([-1.0, 1.0, -1.0], dtype=v.dtype)
             parts.append(v)
         ext = torch.cat([parts[0], ext, parts[1]], dim=ax)
     return ext
@@ -302,7 +306,7 @@ def tau_weights(setup, gas, dt, C):
     grid = setup.grid
     u = gas["u"]
     aE = gas["alpha_a"] + gas["alpha_s"]
-    ue = _gas_ghosts(u, grid)                       # [.., 3]
+    ue = _gas_ghosts(u, grid, vector=True)          # [.., 3]
     ae = _gas_ghosts(aE[..., None], grid)[..., 0]
     out = []
     for d in range(grid.ndim):
