@@ -60,7 +60,8 @@ typedef enum {
 } rad_status;
 
 enum { RAD_MINK_CART = 0, RAD_MINK_SPH = 1, RAD_KS_SPH = 2 };
-enum { RAD_BC_PERIODIC = 0, RAD_BC_OUTFLOW = 1, RAD_BC_POLAR = 2 };
+enum { RAD_BC_PERIODIC = 0, RAD_BC_OUTFLOW = 1, RAD_BC_POLAR = 2,
+       RAD_BC_HALO = 3   /* face shared with another block: ghosts from a halo buffer (rad_step_stage) */ };
 enum { RAD_F64 = 0, RAD_F32 = 1 };
 enum { RAD_RECON_DC = 0, RAD_RECON_PLM = 1, RAD_RECON_PPM = 2, RAD_RECON_MAPR = 3 /* angular only */ };
 enum { RAD_COUPLE_THERMAL = 0, RAD_COUPLE_EMISSIVITY = 1, RAD_COUPLE_NONE = 2 };
@@ -236,6 +237,57 @@ int rad_step_noalloc(rad_ctx *ctx, void *I, const rad_gas *gas, double dt,
                      const rad_opts *opts, double *gas_src);
 
 /*
+ * Decomposed domains (the task list of Sec. 2: a block's fluxes need its
+ * neighbours' cells next to every shared face, exchanged before each
+ * stage; Sec. 5 runs one block per GPU).  A context holds one block: its
+ * rad_grid gives the block's own cells and face coordinates, and
+ * RAD_BC_HALO on every face it shares with another block (a face of the
+ * whole domain keeps its own boundary kind; a periodic direction split into
+ * blocks becomes RAD_BC_HALO on the wrapped faces).  A block needs at least
+ * 3 cells across a shared face; a block touching a polar axis must hold the
+ * whole phi range.  rad_step refuses such blocks: they step one stage at a
+ * time so that the halos of the stage-1 result can be exchanged:
+ *
+ *   for each shared face f: rad_halo_pack(ctx, I, prec, d, side, send[f])
+ *   exchange: the neighbour across f receives send[f] as its halo of the
+ *             opposite face (same layout, layer 0 next to the shared face)
+ *   rad_step_stage(ctx, 1, I, gas, dt, opts, src, halo)
+ *   for each shared face f: rad_halo_pack(ctx, NULL, prec, d, side, send[f])
+ *   exchange
+ *   rad_step_stage(ctx, 2, I, gas, dt, opts, src, halo)
+ *
+ * which computes, cell by cell, exactly what rad_step computes on the whole
+ * domain.  The time step is the minimum of every block's rad_cfl_dt.  The
+ * optical-depth weighting (it reads the neighbour's gas) and the adjoint
+ * take single blocks only (RAD_EUNSUPPORTED).
+ */
+/*
+ * One SSP-RK2 stage of rad_step.  stage 1: I (I^0, not modified) and gas->T
+ * -> the context's stage scratch (I^1, T^1; allocated on first use like
+ * rad_step's).  stage 2: the scratch and I -> I^2 written over I, T^2 over
+ * gas->T, and gas_src as rad_step (stage 1 writes its half, stage 2 adds its
+ * share).  halo: 6 device pointers, face (d, side) at 2 d + side, each the
+ * ghost layers of a RAD_BC_HALO face of the stage's input (I for stage 1,
+ * the stage-1 result for stage 2) in rad_halo_pack's layout; entries of
+ * other faces are ignored (halo may be NULL when there are none).  Stage 2
+ * must follow a stage 1 of the same precision on this context.  Same
+ * options, checks and arithmetic as rad_step otherwise.
+ */
+int rad_step_stage(rad_ctx *ctx, int stage, void *I, const rad_gas *gas, double dt,
+                   const rad_opts *opts, double *gas_src, const void *const *halo);
+
+/*
+ * Copy the 3 layers of an intensity array next to face (dim, side) of this
+ * block into buf (device, 16-byte aligned), layer 0 adjacent to the face:
+ *   dim 0: buf[3][n3][n2][n_ang_padded]   dim 1: buf[3][n3][n1][n_ang_padded]
+ *   dim 2: buf[3][n2][n1][n_ang_padded]
+ * I = NULL packs the context's stage-1 result (after rad_step_stage(.., 1, ..)
+ * of this precision).  dim must carry fluxes and have >= 3 cells.
+ * Asynchronous.
+ */
+int rad_halo_pack(rad_ctx *ctx, const void *I, int precision, int dim, int side, void *buf);
+
+/*
  * Moments R^{AB} = sum_n I_n n^A n^B dOmega_n of every cell, written as 10
  * components [cell][10] in the order 00 01 02 03 11 12 13 22 23 33.
  * precision: element type of I (and of R for RAD_MOM_BF16X3, which writes
@@ -322,6 +374,15 @@ int rad_check(rad_ctx *ctx);
  * RAD_ECUDA ("a device wait timed out").  The context stays usable.
  * Asynchronous; RAD_EINVAL for a bad duration. */
 int rad_selftest_wait(rad_ctx *ctx, double seconds);
+
+/* Measured FP64 fused multiply-add rate of the current device, in TFLOP/s
+ * (no paper counterpart: the denominator for the FP64 stage kernels, which
+ * the FP64 pipe bounds rather than HBM).  Every SM runs independent DFMA
+ * chains; the best of three launches of about seconds/3 each (CUDA events)
+ * is returned.  0 < seconds <= 30.  Synchronous, on the legacy default
+ * stream; allocates and frees a small output buffer.  Reads no clock or
+ * setting of the GPU and changes none. */
+int rad_fp64_fma_rate(double seconds, double *tflops_out);
 
 #ifdef __cplusplus
 }

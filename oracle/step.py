@@ -39,9 +39,10 @@ class Opts:
                                 # | 'mapr' (minimum-angle planes on a geodesic grid)
 
 
-def operator_L(I, setup, opts, tau=None):
-    """L(I) = -(div_space + div_angle), Eq. radiation_integral without sources."""
-    Ie = TR.fill_ghosts(I, setup.grid, setup.ang.perm_pi2)
+def operator_L(I, setup, opts, tau=None, halos=None):
+    """L(I) = -(div_space + div_angle), Eq. radiation_integral without sources;
+    halos: ghost layers of faces shared with other blocks (fill_ghosts)."""
+    Ie = TR.fill_ghosts(I, setup.grid, setup.ang.perm_pi2, halos)
     divS = TR.spatial_divergence(Ie, setup, opts.recon, tau)
     divA = TR.angular_divergence(I, setup, opts.recon_ang)
     return -(divS + divA)
@@ -58,15 +59,21 @@ def to_primitive(U, setup, mask):
     return torch.where(mask, torch.zeros_like(U), U / torch.where(mask, torch.ones_like(U), setup.f))
 
 
-def rk2_step(I0, T0, gas, dt, setup, opts):
-    """One full step.  Returns (I2, T2, src [.., 4], ok)."""
+def rk2_step(I0, T0, gas, dt, setup, opts, exchange=None):
+    """One full step.  Returns (I2, T2, src [.., 4], ok).
+
+    exchange: for a block of a decomposed domain (faces with the 'halo'
+    boundary), a callable taking the stage's input intensities and returning
+    the ghost layers of those faces from the neighbouring blocks (the ghost
+    exchange that precedes each stage's fluxes in the task list of Sec. 2)."""
     f = setup.f
     mask = guard_mask(setup, opts)
     # optical-depth flux weights: frozen gas, the step's dt in both stages
+    assert exchange is None or opts.tau_const == 0.0, "the flux weighting needs the neighbours' gas"
     tau = TR.tau_weights(setup, gas, dt, opts.tau_const) if opts.tau_const > 0.0 else None
     U0 = f * I0
     # stage 1
-    U1s = U0 + dt * operator_L(I0, setup, opts, tau)
+    U1s = U0 + dt * operator_L(I0, setup, opts, tau, exchange(I0) if exchange else None)
     I1s = to_primitive(U1s, setup, mask)
     if opts.couple:
         I1, T1, dR1, ok1 = C.couple(I1s, T0, gas, dt, setup, opts.a_rad, opts.gamma, opts.mode, opts.rad_dom)
@@ -74,7 +81,7 @@ def rk2_step(I0, T0, gas, dt, setup, opts):
         I1, T1, dR1, ok1 = I1s, T0, torch.zeros(T0.shape + (4,), dtype=I0.dtype), torch.ones_like(T0, dtype=torch.bool)
     I1 = torch.where(mask, torch.zeros_like(I1), I1)
     # stage 2
-    U2s = 0.5 * U0 + 0.5 * (f * I1 + dt * operator_L(I1, setup, opts, tau))
+    U2s = 0.5 * U0 + 0.5 * (f * I1 + dt * operator_L(I1, setup, opts, tau, exchange(I1) if exchange else None))
     I2s = to_primitive(U2s, setup, mask)
     Tm = 0.5 * (T0 + T1)
     if opts.couple:

@@ -132,7 +132,18 @@ class Setup:
 
 
 # ------------------------------------------------------------ boundaries
-def fill_ghosts(I, grid, perm):
+def halo_pack(I, grid, d, side):
+    """The NG layers of I next to face (d, side) of the block, as sent to the
+    neighbouring block that shares the face: [NG, <the face's cells in array
+    order>, Na], layer 0 adjacent to the face (the task list of Sec. 2: the
+    ghost exchange between blocks)."""
+    ax = 2 - d
+    N = grid.n[d]
+    idx = [L if side == 0 else N - 1 - L for L in range(NG)]
+    return torch.stack([I.select(ax, q) for q in idx])
+
+
+def fill_ghosts(I, grid, perm, halos=None):
     """Extended array with NG ghost cells per side in every flux dimension.
 
     periodic  ghost takes the cell one period away
@@ -141,6 +152,9 @@ def fill_ghosts(I, grid, perm):
               the active cell across the pole, with angle bin n taking bin
               perm[n] (rotation by pi about the 2-axis of the spherical
               tetrad, under which the geodesic grid is invariant)
+    halo      the face is shared with another block: ghost layer L (0 next to
+              the face) is halos[(d, side)][L], the neighbour's halo_pack of
+              the same face
     """
     N1, N2, N3 = grid.n
     Na = I.shape[-1]
@@ -167,6 +181,11 @@ def fill_ghosts(I, grid, perm):
                     assert d == 1
                     src = gidx if side == 0 else N - 1 - gidx
                     shift, pm = N3 // 2, perm
+                elif kind == "halo":
+                    sl_dst = list(act)
+                    sl_dst[ax] = gpos
+                    Ie[tuple(sl_dst)] = halos[(d, side)][gidx]
+                    continue
                 else:
                     raise ValueError(kind)
                 sl_dst = list(act)

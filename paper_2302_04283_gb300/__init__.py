@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "librad.so")
 RAD_OK, RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA, RAD_ENOCONV, RAD_ENONFINITE, RAD_ESTATE, RAD_EUNSUPPORTED = \
     0, -1, -2, -3, -4, -5, -6, -7
 RAD_MINK_CART, RAD_MINK_SPH, RAD_KS_SPH = 0, 1, 2
-RAD_BC_PERIODIC, RAD_BC_OUTFLOW, RAD_BC_POLAR = 0, 1, 2
+RAD_BC_PERIODIC, RAD_BC_OUTFLOW, RAD_BC_POLAR, RAD_BC_HALO = 0, 1, 2, 3
 RAD_F64, RAD_F32 = 0, 1
 RAD_RECON_DC, RAD_RECON_PLM, RAD_RECON_PPM, RAD_RECON_MAPR = 0, 1, 2, 3
 RAD_COUPLE_THERMAL, RAD_COUPLE_EMISSIVITY, RAD_COUPLE_NONE = 0, 1, 2
@@ -29,7 +29,7 @@ RAD_FRAME_TETRAD, RAD_FRAME_COORD, RAD_FRAME_FLUID = 0, 1, 2
 RAD_MOM_SIMT, RAD_MOM_BF16X3 = 0, 1
 
 KIND = {"mink_cart": RAD_MINK_CART, "mink_sph": RAD_MINK_SPH, "ks_sph": RAD_KS_SPH}
-BC = {"periodic": RAD_BC_PERIODIC, "outflow": RAD_BC_OUTFLOW, "polar": RAD_BC_POLAR}
+BC = {"periodic": RAD_BC_PERIODIC, "outflow": RAD_BC_OUTFLOW, "polar": RAD_BC_POLAR, "halo": RAD_BC_HALO}
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _vp = ctypes.c_void_p
@@ -99,6 +99,10 @@ def lib():
                            ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "rad_check": ([_vp], ctypes.c_int),
         "rad_selftest_wait": ([_vp, ctypes.c_double], ctypes.c_int),
+        "rad_fp64_fma_rate": ([ctypes.c_double, P(ctypes.c_double)], ctypes.c_int),
+        "rad_step_stage": ([_vp, ctypes.c_int, _vp, P(rad_gas), ctypes.c_double, P(rad_opts), _vp, _vp],
+                           ctypes.c_int),
+        "rad_halo_pack": ([_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -207,6 +211,23 @@ def rad_step_noalloc(ctx, I, gas, dt, opts, gas_src=None):
                                        _ptr(gas_src)))
 
 
+def rad_step_stage(ctx, stage, I, gas, dt, opts, gas_src=None, halo=None):
+    """One RK2 stage of a block; halo: dict {(d, side): device tensor} of the
+    ghost layers of the block's shared faces (rad_halo_pack layout)."""
+    g = _gas(gas)
+    arr = (ctypes.c_void_p * 6)()
+    for (d, side), t in (halo or {}).items():
+        arr[2 * d + side] = _ptr(t).value if t is not None else None
+    _check(ctx, lib().rad_step_stage(ctx, int(stage), _ptr(I), ctypes.byref(g), float(dt), ctypes.byref(opts),
+                                     _ptr(gas_src), arr))
+
+
+def rad_halo_pack(ctx, I, precision, dim, side, buf):
+    """Pack the 3 layers next to face (dim, side) of I (None: the context's
+    stage-1 result) into buf."""
+    _check(ctx, lib().rad_halo_pack(ctx, _ptr(I), int(precision), int(dim), int(side), _ptr(buf)))
+
+
 def rad_step_host(ctx, items, dt, opts, nsteps, frame, method):
     """items: list of dicts of host (CPU, ideally pinned) tensors with keys
     I, rho, u, alpha_a, alpha_s, eta (or None), T (in/out), R (out) and
@@ -249,6 +270,15 @@ def rad_check(ctx):
 
 def rad_selftest_wait(ctx, seconds):
     _check(ctx, lib().rad_selftest_wait(ctx, float(seconds)))
+
+
+def rad_fp64_fma_rate(seconds=3.0):
+    """Measured FP64 FMA rate of the current GPU in TFLOP/s."""
+    out = ctypes.c_double()
+    st = lib().rad_fp64_fma_rate(float(seconds), ctypes.byref(out))
+    if st != RAD_OK:
+        raise RadError(st, "rad_fp64_fma_rate failed")
+    return out.value
 
 
 def rad_last_error(ctx):

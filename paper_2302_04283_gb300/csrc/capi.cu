@@ -211,7 +211,10 @@ int rad_set_metric(rad_ctx *ctx, const rad_metric *m, const rad_grid *gr) {
       if (!(gr->xf[d][t + 1] > gr->xf[d][t])) return fail(ctx, RAD_EINVAL, "face coordinates must increase");
     for (int s = 0; s < 2; ++s) {
       int bc = s ? gr->bc_hi[d] : gr->bc_lo[d];
-      if (bc < RAD_BC_PERIODIC || bc > RAD_BC_POLAR) return fail(ctx, RAD_EINVAL, "unknown boundary kind");
+      if (bc < RAD_BC_PERIODIC || bc > RAD_BC_HALO) return fail(ctx, RAD_EINVAL, "unknown boundary kind");
+      if (bc == RAD_BC_HALO && d >= gr->ndim) return fail(ctx, RAD_EINVAL, "a shared face needs a flux dimension");
+      if (bc == RAD_BC_HALO && gr->n[d] < rad::kHaloLayers)
+        return fail(ctx, RAD_EINVAL, "a block needs at least 3 cells across a shared face");
       if (bc == RAD_BC_POLAR && (d != 1 || m->kind == RAD_MINK_CART))
         return fail(ctx, RAD_EINVAL, "polar boundaries apply to theta (x2) of a spherical metric only");
     }
@@ -224,6 +227,8 @@ int rad_set_metric(rad_ctx *ctx, const rad_metric *m, const rad_grid *gr) {
     if (std::fabs((x3[t + 1] - x3[t]) - w3) > 1e-12 * std::fabs(w3))
       return fail(ctx, RAD_EUNSUPPORTED, "x3 faces must be uniformly spaced");
   bool polar = gr->bc_lo[1] == RAD_BC_POLAR || gr->bc_hi[1] == RAD_BC_POLAR;
+  if (polar && (gr->bc_lo[2] == RAD_BC_HALO || gr->bc_hi[2] == RAD_BC_HALO))
+    return fail(ctx, RAD_EUNSUPPORTED, "a block on a polar axis must hold the whole phi range (no shared x3 faces)");
   if (polar) {
     if (gr->n[1] < 2) return fail(ctx, RAD_EINVAL, "polar boundaries need n[1] >= 2");
     if (gr->n[2] > 1 && (gr->n[2] % 2 != 0)) return fail(ctx, RAD_EINVAL, "polar boundaries need an even n[2]");
@@ -310,11 +315,22 @@ static int check_opts(rad_ctx *ctx, const rad_opts *o) {
 // The host-side checks every RK2 step entry (rad_step, rad_step_noalloc)
 // makes before anything is launched: options, gas fields, the intensity
 // pointer, dt, the bin count and the 32-bit element index.
-int rad::check_step_args(rad_ctx *ctx, const void *I, const rad_gas *gas, double dt, const rad_opts *o) {
+static bool has_halo(const rad::DevGeom &G) {
+  for (int d = 0; d < 3; ++d)
+    if (G.bc_lo[d] == RAD_BC_HALO || G.bc_hi[d] == RAD_BC_HALO) return true;
+  return false;
+}
+
+int rad::check_step_args(rad_ctx *ctx, const void *I, const rad_gas *gas, double dt, const rad_opts *o,
+                         bool staged) {
   if (!ctx) return RAD_EINVAL;
   if (!ctx->have_metric) return fail(ctx, RAD_ESTATE, "rad_set_metric has not been called");
+  if (!staged && has_halo(ctx->geom))
+    return fail(ctx, RAD_ESTATE, "a block with faces shared with other blocks (RAD_BC_HALO) steps with rad_step_stage");
   int st = check_opts(ctx, o);
   if (st != RAD_OK) return st;
+  if (has_halo(ctx->geom) && o->tau_const > 0.0)
+    return fail(ctx, RAD_EUNSUPPORTED, "the optical-depth weighting reads the neighbour's gas: single blocks only");
   if ((st = check_gas(ctx, gas, o, true)) != RAD_OK) return st;
   if (!I || !aligned16(I)) return fail(ctx, RAD_EINVAL, "I must be a 16-byte aligned device pointer");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, RAD_EINVAL, "dt must be finite and > 0");
@@ -329,9 +345,9 @@ int rad::check_step_args(rad_ctx *ctx, const void *I, const rad_gas *gas, double
 
 extern "C" {
 
-int rad_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src) {
-  int st = rad::check_step_args(ctx, I, gas, dt, o);
-  if (st != RAD_OK) return st;
+// The stage scratch of rad_step / rad_step_stage (one intensity array and one
+// temperature per cell), grown on demand.
+static int ensure_scratch(rad_ctx *ctx, const rad_opts *o) {
   const rad::DevGeom &G = ctx->geom;
   size_t ncell = (size_t)G.n[0] * G.n[1] * G.n[2];
   size_t esz = o->precision == RAD_F32 ? 4 : 8;
@@ -353,8 +369,61 @@ int rad_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opt
       return fail(ctx, RAD_ENOMEM, "stage scratch allocation failed");
     ctx->scratch_T_count = ncell;
   }
+  return RAD_OK;
+}
+
+int rad_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src) {
+  int st = rad::check_step_args(ctx, I, gas, dt, o);
+  if (st != RAD_OK) return st;
+  if ((st = ensure_scratch(ctx, o)) != RAD_OK) return st;
+  ctx->stage1_prec = -1;    // the scratch no longer holds a rad_step_stage stage-1 result
   std::string err;
   st = rad::launch_step(ctx, I, gas, dt, o, gas_src, ctx->scratch_I, ctx->scratch_T, err);
+  return st == RAD_OK ? st : fail(ctx, st, err);
+}
+
+int rad_step_stage(rad_ctx *ctx, int stage, void *I, const rad_gas *gas, double dt, const rad_opts *o,
+                   double *gas_src, const void *const *halo) {
+  int st = rad::check_step_args(ctx, I, gas, dt, o, true);
+  if (st != RAD_OK) return st;
+  if (stage != 1 && stage != 2) return fail(ctx, RAD_EINVAL, "stage must be 1 or 2");
+  const rad::DevGeom &G = ctx->geom;
+  for (int d = 0; d < 3; ++d)
+    for (int side = 0; side < 2; ++side)
+      if ((side ? G.bc_hi[d] : G.bc_lo[d]) == RAD_BC_HALO && (!halo || !halo[2 * d + side] ||
+                                                               !aligned16(halo[2 * d + side])))
+        return fail(ctx, RAD_EINVAL, "every shared face needs a 16-byte aligned halo buffer");
+  const size_t ncell = (size_t)G.n[0] * G.n[1] * G.n[2];
+  const size_t esz = o->precision == RAD_F32 ? 4 : 8;
+  if (stage == 1) {
+    if ((st = ensure_scratch(ctx, o)) != RAD_OK) return st;
+    ctx->stage1_prec = o->precision;
+  } else if (ctx->stage1_prec != o->precision || ctx->scratch_I_bytes < ncell * ctx->ang.n_ap * esz ||
+             ctx->scratch_T_count < ncell) {
+    return fail(ctx, RAD_ESTATE, "stage 2 needs a stage 1 of the same precision on this context first");
+  }
+  std::string err;
+  st = rad::launch_stage_s(ctx, stage, I, gas, dt, o, gas_src, ctx->scratch_I, ctx->scratch_T, halo, err);
+  return st == RAD_OK ? st : fail(ctx, st, err);
+}
+
+int rad_halo_pack(rad_ctx *ctx, const void *I, int precision, int dim, int side, void *buf) {
+  if (!ctx) return RAD_EINVAL;
+  if (!ctx->have_metric) return fail(ctx, RAD_ESTATE, "rad_set_metric has not been called");
+  if (precision != RAD_F64 && precision != RAD_F32) return fail(ctx, RAD_EINVAL, "bad precision");
+  if (dim < 0 || dim >= ctx->geom.ndim || (side != 0 && side != 1))
+    return fail(ctx, RAD_EINVAL, "dim must be a flux dimension and side 0 or 1");
+  if (ctx->geom.n[dim] < rad::kHaloLayers) return fail(ctx, RAD_EINVAL, "fewer than 3 cells across the face");
+  if (!buf || !aligned16(buf) || (I && !aligned16(I))) return fail(ctx, RAD_EINVAL, "buffers must be 16-byte aligned");
+  if (!I) {
+    const rad::DevGeom &G = ctx->geom;
+    const size_t need = (size_t)G.n[0] * G.n[1] * G.n[2] * ctx->ang.n_ap * (precision == RAD_F32 ? 4 : 8);
+    if (!ctx->scratch_I || ctx->scratch_I_bytes < need || ctx->stage1_prec != precision)
+      return fail(ctx, RAD_ESTATE, "no stage-1 result of this precision on this context");
+    I = ctx->scratch_I;
+  }
+  std::string err;
+  int st = rad::launch_halo_pack(ctx, I, precision, dim, side, buf, err);
   return st == RAD_OK ? st : fail(ctx, st, err);
 }
 
@@ -384,6 +453,7 @@ int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double d
   if ((st = check_gas(ctx, gas, o, true)) != RAD_OK) return st;
   if (o->rad_dom)
     return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers the coupling at the gas velocity (rad_dom = 0)");
+  if (has_halo(ctx->geom)) return fail(ctx, RAD_EUNSUPPORTED, "the adjoint steps single blocks (no RAD_BC_HALO faces)");
   if (!I_n || !lam_np1 || !lam_n || !g_aa || !g_as) return fail(ctx, RAD_EINVAL, "null argument");
   if (!(dt > 0.0)) return fail(ctx, RAD_EINVAL, "dt must be > 0");
   if (ctx->ang.n_ang > rad::kMaxBinsStep)

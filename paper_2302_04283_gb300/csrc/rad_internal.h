@@ -128,6 +128,7 @@ struct rad_ctx {
   size_t scratch_I_bytes = 0;
   double *scratch_T = nullptr;
   size_t scratch_T_count = 0;
+  int stage1_prec = -1;         // precision of the last rad_step_stage stage 1 (its result is in scratch_I)
   // rad_step_adjoint scratch
   void *adj_buf = nullptr;
   size_t adj_bytes = 0;
@@ -149,7 +150,9 @@ struct rad_ctx {
 namespace rad {
 
 // capi.cu: the checks shared by every RK2 step entry point (sets ctx->last_error)
-int check_step_args(rad_ctx *ctx, const void *I, const rad_gas *gas, double dt, const rad_opts *o);
+// (staged: rad_step_stage, which takes blocks with faces shared with other blocks)
+int check_step_args(rad_ctx *ctx, const void *I, const rad_gas *gas, double dt, const rad_opts *o,
+                    bool staged = false);
 
 // geom.cu
 int compute_geometry(rad_ctx *ctx, std::string &err);
@@ -159,6 +162,14 @@ void free_geometry(DevGeom &g);
 struct StageArgs;
 int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opts *opts,
                 double *gas_src, void *scratch_I, double *scratch_T, std::string &err);
+// one RK2 stage (1: I -> scratch, 2: scratch + I -> I); halo: the ghost rows of
+// faces shared with other blocks (6 pointers, face (d, side) at 2 d + side), or null
+int launch_stage_s(rad_ctx *ctx, int stage, void *I, const rad_gas *gas, double dt, const rad_opts *opts,
+                   double *gas_src, void *scratch_I, double *scratch_T, const void *const *halo,
+                   std::string &err);
+// rad_halo_pack: the kHaloLayers layers of I next to face (dim, side) into buf
+int launch_halo_pack(rad_ctx *ctx, const void *I, int precision, int dim, int side, void *buf, std::string &err);
+constexpr int kHaloLayers = 3;   // the widest stencil (PPM) reaches three cells
 int launch_cfl(rad_ctx *ctx, double cfl, double *dt_out, std::string &err);
 cudaError_t launch_wait_selftest(rad_ctx *ctx, double seconds);
 

@@ -159,6 +159,7 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
   a.inv_gm1 = 1.0 / (o->gamma - 1.0);
   a.tau_const = o->tau_const;
   a.err = ctx->err_word;
+  for (int f = 0; f < 6; ++f) a.halo[f] = nullptr;
   return a;
 }
 
@@ -185,8 +186,8 @@ int check_stage(const StageArgs &a, bool f32, std::string &err) {
   return RAD_OK;
 }
 
-int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src,
-                void *scratch_I, double *scratch_T, std::string &err) {
+int launch_stage_s(rad_ctx *ctx, int stage, void *I, const rad_gas *gas, double dt, const rad_opts *o,
+                   double *gas_src, void *scratch_I, double *scratch_T, const void *const *halo, std::string &err) {
   StageArgs a = make_stage_args(ctx, gas, dt, o, gas_src);
   const bool f32 = o->precision == RAD_F32;
   const bool ang = ctx->geom.kind != RAD_MINK_CART;
@@ -194,42 +195,51 @@ int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_
     const int rc = check_stage(a, f32, err);
     if (rc != RAD_OK) return rc;
   }
+  if (halo)
+    for (int f = 0; f < 6; ++f) a.halo[f] = halo[f];
   // rad_dom: each stage is the transport-only stage kernel (I* with the
   // guard applied, T- in Tout) followed by the coupling kernel with the
   // radiation-dominated velocity substitution, in place
   const bool rd = o->rad_dom != 0;
   if (rd) a.mode = RAD_COUPLE_NONE;
-  // stage 1: I^0 -> I^1 (scratch), T^0 -> T^1 (scratch)
-  a.Iprev = I;
-  a.I0 = I;
-  a.Iout = scratch_I;
-  a.T0 = gas->T;
-  a.T1 = nullptr;
-  a.Tout = scratch_T;
-  a.stage2 = 0;
-  a.dts = dt;
-  cudaError_t ce = launch_stage(a, f32, ang, ctx->stream);
-  if (ce == cudaSuccess && rd) ce = launch_couple_rd(a, f32, scratch_T, scratch_T, ctx->stream);
-  if (ce != cudaSuccess) {
-    err = std::string("stage 1 launch failed: ") + cudaGetErrorString(ce);
-    return RAD_ECUDA;
+  cudaError_t ce;
+  if (stage == 1) {
+    // stage 1: I^0 -> I^1 (scratch), T^0 -> T^1 (scratch)
+    a.Iprev = I;
+    a.I0 = I;
+    a.Iout = scratch_I;
+    a.T0 = gas->T;
+    a.T1 = nullptr;
+    a.Tout = scratch_T;
+    a.stage2 = 0;
+    a.dts = dt;
+    ce = launch_stage(a, f32, ang, ctx->stream);
+    if (ce == cudaSuccess && rd) ce = launch_couple_rd(a, f32, scratch_T, scratch_T, ctx->stream);
+  } else {
+    // stage 2: I^1 (+ own I^0) -> I^2 written over I^0; T -> gas->T
+    a.Iprev = scratch_I;
+    a.I0 = I;
+    a.Iout = I;
+    a.T0 = gas->T;
+    a.T1 = scratch_T;
+    a.Tout = gas->T;
+    a.stage2 = 1;
+    a.dts = 0.5 * dt;
+    ce = launch_stage(a, f32, ang, ctx->stream);
+    if (ce == cudaSuccess && rd) ce = launch_couple_rd(a, f32, gas->T, gas->T, ctx->stream);
   }
-  // stage 2: I^1 (+ own I^0) -> I^2 written over I^0; T -> gas->T
-  a.Iprev = scratch_I;
-  a.I0 = I;
-  a.Iout = I;
-  a.T0 = gas->T;
-  a.T1 = scratch_T;
-  a.Tout = gas->T;
-  a.stage2 = 1;
-  a.dts = 0.5 * dt;
-  ce = launch_stage(a, f32, ang, ctx->stream);
-  if (ce == cudaSuccess && rd) ce = launch_couple_rd(a, f32, gas->T, gas->T, ctx->stream);
   if (ce != cudaSuccess) {
-    err = std::string("stage 2 launch failed: ") + cudaGetErrorString(ce);
+    err = std::string(stage == 1 ? "stage 1" : "stage 2") + " launch failed: " + cudaGetErrorString(ce);
     return RAD_ECUDA;
   }
   return RAD_OK;
+}
+
+int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src,
+                void *scratch_I, double *scratch_T, std::string &err) {
+  int st = launch_stage_s(ctx, 1, I, gas, dt, o, gas_src, scratch_I, scratch_T, nullptr, err);
+  if (st == RAD_OK) st = launch_stage_s(ctx, 2, I, gas, dt, o, gas_src, scratch_I, scratch_T, nullptr, err);
+  return st;
 }
 
 int launch_cfl(rad_ctx *ctx, double cfl, double *dt_out, std::string &err) {

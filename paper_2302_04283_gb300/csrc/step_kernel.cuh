@@ -82,6 +82,7 @@ struct StageArgs {
   double inv_gm1;          // 1 / (gamma - 1)
   double tau_const;       // C of the optical-depth flux weighting (0: free streaming)
   int *err;
+  const void *halo[6];     // ghost rows of faces shared with other blocks: face (d, side) at 2 d + side
 };
 
 StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src);
@@ -232,21 +233,45 @@ struct Nbr {
   int polar;          // read bin perm[n]
 };
 
-__device__ __forceinline__ int wrap_idx(int x, int n, int bc_lo, int bc_hi, int &polar) {
-  polar = 0;
+// Index of the cell a stencil position x (possibly outside 0..n-1) reads.
+// kind: 0 a cell of this block (periodic wrap, outflow clamp), 1 the polar
+// mirror (theta -> -theta: the caller shifts phi by pi and permutes the
+// bins), 2 / 3 a ghost of a lower / upper face shared with another block
+// (RAD_BC_HALO): the value returned is then the ghost layer, 0 next to the
+// face.
+__device__ __forceinline__ int wrap_idx(int x, int n, int bc_lo, int bc_hi, int &kind) {
+  kind = 0;
   if (x < 0) {
     if (bc_lo == RAD_BC_PERIODIC) return ((x % n) + n) % n;
     if (bc_lo == RAD_BC_OUTFLOW) return 0;
-    polar = 1;
+    kind = bc_lo == RAD_BC_HALO ? 2 : 1;
     return -1 - x;
   }
   if (x >= n) {
     if (bc_hi == RAD_BC_PERIODIC) return x % n;
     if (bc_hi == RAD_BC_OUTFLOW) return n - 1;
-    polar = 1;
+    if (bc_hi == RAD_BC_HALO) {
+      kind = 3;
+      return x - n;
+    }
+    kind = 1;
     return 2 * n - 1 - x;
   }
   return x;
+}
+
+// Row of ghost layer `layer` of face (d, side) in that face's halo buffer
+// (rad_halo_pack's layout): [layer][k][j] for x1 faces, [layer][k][i] for x2
+// faces, [layer][j][i] for x3 faces, rows of nap elements.
+template <typename R>
+__device__ __forceinline__ const R *halo_row(const void *const *halo, int n1, int n2, int n3, int d, int side,
+                                             int layer, int i, int j, int k, int nap) {
+  const R *b = (const R *)halo[2 * d + side];
+  size_t r;
+  if (d == 0) r = ((size_t)layer * n3 + k) * n2 + j;
+  else if (d == 1) r = ((size_t)layer * n3 + k) * n1 + i;
+  else r = ((size_t)layer * n2 + j) * n1 + i;
+  return b + r * nap;
 }
 
 // ---------------------------------------------------------------- pairs
@@ -551,7 +576,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       if (d == 0) ii = wrap_idx(i + sg, a.n1, a.bc_lo[0], a.bc_hi[0], pol);
       if (d == 1) {
         jj = wrap_idx(j + sg, a.n2, a.bc_lo[1], a.bc_hi[1], pol);
-        if (pol && a.n3 > 1) kk = (k + a.n3 / 2) % a.n3;
+        if (pol == 1 && a.n3 > 1) kk = (k + a.n3 / 2) % a.n3;
       }
       if (d == 2) kk = wrap_idx(k + sg, a.n3, a.bc_lo[2], a.bc_hi[2], pol);
       const unsigned cell = (unsigned)k * ncol + col;
@@ -722,12 +747,15 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   // this column's row at k+h (x3 window) and, in stage 2, this column's row
   // of I^0.  Slots: 0..2h x1 block (h = own), then the x2 rows j-h..j+h
   // without j, then own k+h, then I^0.
-  int xs[X1N], yj[X2N], ypol[X2N];
+  // row kinds (wrap_idx): x1 rows 0 or a halo side (2, 3); x2 rows 0, the
+  // polar mirror (1) or a halo side
+  int xs[X1N], xk[X1N], yj[X2N], ypol[X2N];
   bool x1contig = true;
   for (int q = 0; q < X1N; ++q) {
-    int pol;
-    xs[q] = q == H ? i : wrap_idx(i + q - H, a.n1, a.bc_lo[0], a.bc_hi[0], pol);
-    if (xs[q] != i + q - H) x1contig = false;
+    int kind = 0;
+    xs[q] = q == H ? i : wrap_idx(i + q - H, a.n1, a.bc_lo[0], a.bc_hi[0], kind);
+    xk[q] = kind;
+    if (xs[q] != i + q - H || kind) x1contig = false;
   }
   bool anypol = false;
   for (int q = 0; q < X2N; ++q) {
@@ -735,16 +763,19 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
     const int o = q < H ? q - H : q - H + 1;
     yj[q] = a.ndim >= 2 ? wrap_idx(j + o, a.n2, a.bc_lo[1], a.bc_hi[1], pol) : j;
     ypol[q] = pol;
-    anypol |= pol != 0;
+    anypol |= pol == 1;
   }
   const bool d3 = a.ndim >= 3;
   const size_t rowb = (size_t)nap * sizeof(R);
-  auto kidx = [&](int k) {
-    int pol;
-    return wrap_idx(k, a.n3, a.bc_lo[2], a.bc_hi[2], pol);
-  };
   auto rowp = [&](const R *base, int ii, int jj, int kk) {
     return base + ((size_t)kk * ncol + (size_t)jj * a.n1 + ii) * nap;
+  };
+  // this column's row at plane k (any k: wrapped, clamped or a halo row)
+  auto krow = [&](int k) -> const R * {
+    int kind;
+    const int kk = wrap_idx(k, a.n3, a.bc_lo[2], a.bc_hi[2], kind);
+    if (kind >= 2) return halo_row<R>(a.halo, a.n1, a.n2, a.n3, 2, kind - 2, kk, i, j, 0, nap);
+    return rowp(Ip, i, j, kk);
   };
   auto produce = [&](int c, int st) {   // issue the copies of cell k0 + c into ring stage st
     const int k = k0 + c;
@@ -755,16 +786,26 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
     if (x1contig) {
       bulk_g2s(dst, rowp(Ip, i - H, j, k), (uint32_t)(X1N * rowb), &bars[st]);
     } else {
-      for (int q = 0; q < X1N; ++q) bulk_g2s(dst + q * nap, rowp(Ip, xs[q], j, k), (uint32_t)rowb, &bars[st]);
+      for (int q = 0; q < X1N; ++q) {
+        const R *src = xk[q] >= 2 ? halo_row<R>(a.halo, a.n1, a.n2, a.n3, 0, xk[q] - 2, xs[q], 0, j, k, nap)
+                                  : rowp(Ip, xs[q], j, k);
+        bulk_g2s(dst + q * nap, src, (uint32_t)rowb, &bars[st]);
+      }
     }
     if (a.ndim >= 2) {
       for (int q = 0; q < X2N; ++q) {
-        int kk = k;
-        if (ypol[q] && a.n3 > 1) kk = (k + a.n3 / 2) % a.n3;
-        bulk_g2s(dst + (SX2 + q) * nap, rowp(Ip, i, yj[q], kk), (uint32_t)rowb, &bars[st]);
+        const R *src;
+        if (ypol[q] >= 2) {
+          src = halo_row<R>(a.halo, a.n1, a.n2, a.n3, 1, ypol[q] - 2, yj[q], i, 0, k, nap);
+        } else {
+          int kk = k;
+          if (ypol[q] == 1 && a.n3 > 1) kk = (k + a.n3 / 2) % a.n3;
+          src = rowp(Ip, i, yj[q], kk);
+        }
+        bulk_g2s(dst + (SX2 + q) * nap, src, (uint32_t)rowb, &bars[st]);
       }
     }
-    if (d3) bulk_g2s(dst + SX3 * nap, rowp(Ip, i, j, kidx(k + H)), (uint32_t)rowb, &bars[st]);
+    if (d3) bulk_g2s(dst + SX3 * nap, krow(k + H), (uint32_t)rowb, &bars[st]);
     if (ST2) bulk_g2s(dst + SI0 * nap, rowp(I0, i, j, k), (uint32_t)rowb, &bars[st]);
   };
   const int p0 = act0 ? a.perm[b0] : 0, p1 = act1 ? a.perm[b0 + 1] : 0;
@@ -810,13 +851,13 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   for (int q = 0; q < 6; ++q) pw[q] = zero;
   if (ppm && cons && d3) {
 #pragma unroll
-    for (int q = 0; q < 6; ++q) pw[q] = __ldg((const V *)(Ip + (unsigned)kidx(k0 - 3 + q) * strideK + own));
+    for (int q = 0; q < 6; ++q) pw[q] = __ldg((const V *)(krow(k0 - 3 + q) + bb));
   }
   if (!ppm && cons && d3) {
-    w0 = __ldg((const V *)(Ip + (unsigned)kidx(k0 - 2) * strideK + own));
-    w1 = __ldg((const V *)(Ip + (unsigned)kidx(k0 - 1) * strideK + own));
-    w2 = __ldg((const V *)(Ip + (unsigned)kidx(k0) * strideK + own));
-    w3 = __ldg((const V *)(Ip + (unsigned)kidx(k0 + 1) * strideK + own));
+    w0 = __ldg((const V *)(krow(k0 - 2) + bb));
+    w1 = __ldg((const V *)(krow(k0 - 1) + bb));
+    w2 = __ldg((const V *)(krow(k0) + bb));
+    w3 = __ldg((const V *)(krow(k0 + 1) + bb));
     if (plm) {
       qa = vl2<R>(w0, w1, w2);
       qb = vl2<R>(w1, w2, w3);
@@ -895,7 +936,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
 #pragma unroll
       for (int q = 0; q < X2N; ++q) {
         const R *row = sr + (SX2 + q) * nap;
-        v[q < H ? q : q + 1] = (ANG && anypol && ypol[q]) ? P::mk(row[p0], row[p1]) : sv(row);
+        v[q < H ? q : q + 1] = (ANG && anypol && ypol[q] == 1) ? P::mk(row[p0], row[p1]) : sv(row);
       }
       V loL, loR, hiL, hiR;
       ppm_states<R>(v, loL, loR, hiL, hiR);
@@ -905,7 +946,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const R *row = sr + (SX2 + q) * nap;
-        yv[q] = (ANG && anypol && ypol[q]) ? P::mk(row[p0], row[p1]) : sv(row);
+        yv[q] = (ANG && anypol && ypol[q] == 1) ? P::mk(row[p0], row[p1]) : sv(row);
       }
       V sm = zero, sc = zero, sp = zero;
       if (plm) {

@@ -178,8 +178,12 @@ def make(name, n=None, level=None, seed=None, with_intensity=True, latlong=None)
         w["alpha_a"] = (10.0 ** fa)[None].copy()
         w["alpha_s"] = (10.0 ** fs)[None].copy()
         w["eta"] = ((10.0 ** fe) / (4 * math.pi))[None].copy()
+    # position of the generator where the intensity draws start (intensity_rows
+    # draws any rows of I0 from here without forming the whole array)
+    w["_rng_I0"] = rng.bit_generator.state
+    w["n_ang"] = n_ang(level) if latlong is None else latlong[0] * latlong[1]
     if with_intensity:
-        na = n_ang(level) if latlong is None else latlong[0] * latlong[1]
+        na = w["n_ang"]
         U = rng.uniform(-1.0, 1.0, shape + (na,))
         if name == "adjoint2d":
             base = np.full(shape, 1.0 / (4 * math.pi))
@@ -187,6 +191,33 @@ def make(name, n=None, level=None, seed=None, with_intensity=True, latlong=None)
             base = w["T"] ** 4 / (4 * math.pi)
         w["I0"] = base[..., None] * (1.0 + 0.1 * U)
     return w
+
+
+def _base_intensity(w, k, j):
+    """a_rad T^4 / 4 pi (1 / 4 pi for adjoint2d) of the x1 row (k, j)."""
+    if w["name"] == "adjoint2d":
+        return np.full(w["n"][0], 1.0 / (4 * math.pi))
+    return w["T"][k, j] ** 4 / (4 * math.pi)
+
+
+def intensity_rows(w, k, j=None):
+    """Rows of the initial intensity I0 without forming the whole array: the
+    x1 row (k, j) as [n1, n_ang], or with j None the whole x3 slab k as
+    [n2, n1, n_ang].  Equal to make(...)["I0"][k, j] / ["I0"][k]: every
+    uniform draw takes one 64-bit output of PCG64, so the generator is
+    advanced to the row's first element."""
+    n1, n2, _ = w["n"]
+    na = w["n_ang"]
+    bg = np.random.PCG64()
+    bg.state = w["_rng_I0"]
+    if j is None:
+        bg.advance(k * n2 * n1 * na)
+        U = np.random.Generator(bg).uniform(-1.0, 1.0, (n2, n1, na))
+        base = np.stack([_base_intensity(w, k, jj) for jj in range(n2)])
+        return base[..., None] * (1.0 + 0.1 * U)
+    bg.advance((k * n2 + j) * n1 * na)
+    U = np.random.Generator(bg).uniform(-1.0, 1.0, (n1, na))
+    return _base_intensity(w, k, j)[:, None] * (1.0 + 0.1 * U)
 
 
 def fd_cells(w, count=16):
