@@ -6,6 +6,8 @@ stationary_metric) and independent of x3.  Three spacetimes:
   'mink_cart'  Minkowski, Cartesian (x, y, z)
   'mink_sph'   Minkowski, spherical (r, theta, phi)        (tests only)
   'ks_sph'     Kerr in spherical Kerr-Schild (r, theta, phi), M = 1, spin a
+  'schw_sph'   Schwarzschild in Schwarzschild coordinates, M = 1 (tests only:
+               its normal observers are the static ones)
 
 Tetrad (Eq. tetrad and the normal-observer condition below it):
   e_0hat^alpha = -alpha g^{0 alpha}; the spatial legs have zero time
@@ -31,7 +33,7 @@ from torch.func import jacfwd, vmap
 
 from . import DTYPE
 
-KINDS = ("mink_cart", "mink_sph", "ks_sph")
+KINDS = ("mink_cart", "mink_sph", "ks_sph", "schw_sph")
 
 
 def metric(kind, a, x):
@@ -45,6 +47,11 @@ def metric(kind, a, x):
         s = torch.sin(th)
         rows = [[-one, z, z, z], [z, one, z, z], [z, z, r * r, z],
                 [z, z, z, r * r * s * s]]
+    elif kind == "schw_sph":
+        r, th = x[0], x[1]
+        s = torch.sin(th)
+        f = 1.0 - 2.0 / r
+        rows = [[-f, z, z, z], [z, 1.0 / f, z, z], [z, z, r * r, z], [z, z, z, r * r * s * s]]
     elif kind == "ks_sph":
         r, th = x[0], x[1]
         s, c = torch.sin(th), torch.cos(th)
