@@ -237,6 +237,52 @@ int rad_step_noalloc(rad_ctx *ctx, void *I, const rad_gas *gas, double dt,
                      const rad_opts *opts, double *gas_src);
 
 /*
+ * Gas update from the step's radiation source (end of Sec. 2.5: the change
+ * of R^0_mu produced by the coupling is taken from the gas).  rho, u
+ * ([cell][3], tetrad-frame u^ihat) and T (device FP64, per cell of this
+ * context's grid) hold the gas state the step started from (keep a copy of
+ * gas->T before rad_step, which overwrites it) and receive the state after
+ * the source: T^0_mu = w u^0 u_mu + p delta^0_mu (ideal gas, p = rho T,
+ * w = rho + gamma p / (gamma - 1)) gains src_mu, summed over n_src arrays
+ * [n_src][cell][4] (rad_step's gas_src; n_src = n_groups for multigroup),
+ * while rho u^0 is kept, and (rho, u, T) are recovered from the new
+ * conserved state (one pressure equation per cell, solved in FP64).  A
+ * cell whose new state is not physical (E <= (S^2 + D^2)^(1/2) in the
+ * normal observer's frame) is left unchanged and sets the sticky
+ * RAD_ENOCONV.  1 < gamma <= 2.  Asynchronous.
+ */
+int rad_gas_update(rad_ctx *ctx, double *rho, double *u, double *T, const double *src, int n_src,
+                   double gamma);
+
+/*
+ * Multigroup transport (Sec. 2.2, Eq. radiation_integral_frequency): the
+ * intensity is resolved in n_groups intervals of the tetrad-frame
+ * frequency, nu_edges[0] < ... < nu_edges[n_groups] (host array; the first
+ * >= 0, every edge finite except possibly the last, which may be +inf).
+ * Each group's intensity (the integral of I_nu over its interval) takes the
+ * gray spatial and angular fluxes plus the difference of the frequency
+ * fluxes n^nu n_0 I_nu at its edges, n^nu = -nu omega^0hat_{AB} n^A n^B
+ * (cell-centre geometry), donor cell in frequency: the upwind group's mean
+ * I_g / dnu_g, the lower group where n^nu > 0, the upper where n^nu < 0; the
+ * end edges pass radiation out of the resolved range and none in, and an
+ * edge at 0 or infinity carries nothing.  While groups are set:
+ *   - rad_step takes I as [n_groups][n3][n2][n1][n_ang_padded], gas->alpha_a,
+ *     alpha_s and eta as [n_groups][n3][n2][n1] (rho, u and T per cell as
+ *     before) and gas_src as [n_groups][n3][n2][n1][4];
+ *   - coupling is RAD_COUPLE_EMISSIVITY (each group coupled on its own with
+ *     the gray formulas; the gas temperature stays fixed) or
+ *     RAD_COUPLE_NONE; RAD_COUPLE_THERMAL and rad_dom give RAD_EUNSUPPORTED,
+ *     as do rad_step_stage, rad_step_noalloc, rad_step_host and
+ *     rad_step_adjoint;
+ *   - rad_cfl_dt also bounds dt by n^0 dnu_g / (nu_{g+1} |omega^0hat n n|) for
+ *     every finite group;
+ *   - rad_moments and rad_loss_outer take one group's array at a time.
+ * n_groups = 0 returns to gray transport.  One group spanning [0, inf) is
+ * the gray step.  Synchronous.
+ */
+int rad_set_groups(rad_ctx *ctx, int n_groups, const double *nu_edges);
+
+/*
  * Decomposed domains (the task list of Sec. 2: a block's fluxes need its
  * neighbours' cells next to every shared face, exchanged before each
  * stage; Sec. 5 runs one block per GPU).  A context holds one block: its

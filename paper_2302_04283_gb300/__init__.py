@@ -103,6 +103,8 @@ def lib():
         "rad_step_stage": ([_vp, ctypes.c_int, _vp, P(rad_gas), ctypes.c_double, P(rad_opts), _vp, _vp],
                            ctypes.c_int),
         "rad_halo_pack": ([_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp], ctypes.c_int),
+        "rad_set_groups": ([_vp, ctypes.c_int, P(ctypes.c_double)], ctypes.c_int),
+        "rad_gas_update": ([_vp, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_double], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -220,6 +222,25 @@ def rad_step_stage(ctx, stage, I, gas, dt, opts, gas_src=None, halo=None):
         arr[2 * d + side] = _ptr(t).value if t is not None else None
     _check(ctx, lib().rad_step_stage(ctx, int(stage), _ptr(I), ctypes.byref(g), float(dt), ctypes.byref(opts),
                                      _ptr(gas_src), arr))
+
+
+def rad_gas_update(ctx, rho, u, T, src, gamma=5.0 / 3.0):
+    """Apply the step's gas source (src: [.., 4] or [n_groups, .., 4]) to the
+    gas state (rho, u, T) the step started from, in place."""
+    per = rho.numel() * 4
+    if src.numel() % per:
+        raise ValueError("src must hold whole [cell][4] arrays")
+    _check(ctx, lib().rad_gas_update(ctx, _ptr(rho), _ptr(u), _ptr(T), _ptr(src), src.numel() // per,
+                                     float(gamma)))
+
+
+def rad_set_groups(ctx, nu_edges):
+    """Multigroup transport with the given frequency edges (n_groups + 1
+    values, increasing, the last may be inf); an empty list returns to gray."""
+    e = [float(x) for x in nu_edges]
+    ng = max(0, len(e) - 1)
+    arr = (ctypes.c_double * max(1, len(e)))(*e)
+    _check(ctx, lib().rad_set_groups(ctx, ng, arr))
 
 
 def rad_halo_pack(ctx, I, precision, dim, side, buf):

@@ -20,7 +20,7 @@ SOURCES = ["angles.cpp", "capi.cu", "geom.cu", "step.cu",
            "moments.cu", "moments_tc.cu", "adjoint.cu", "adjoint_tadj_f32_flat.cu", "adjoint_tadj_f32_ang.cu",
            "adjoint_tadj_f64_flat.cu", "adjoint_tadj_f64_ang.cu",
            "adjoint_tadj_f32_angplm.cu", "adjoint_tadj_f64_angplm.cu",
-           "adjoint_tadj_f32_angmapr.cu", "adjoint_tadj_f64_angmapr.cu", "noalloc.cu", "host_stream.cu", "raddom.cu", "peak.cu", "halo.cu"]
+           "adjoint_tadj_f32_angmapr.cu", "adjoint_tadj_f64_angmapr.cu", "noalloc.cu", "host_stream.cu", "raddom.cu", "peak.cu", "halo.cu", "frequency.cu", "gas.cu"]
 
 
 def _compile(src, extra):

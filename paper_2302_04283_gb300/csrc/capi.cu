@@ -1,5 +1,6 @@
 // C ABI entry points: argument validation, context state, table upload and
 // dispatch to the kernels.  No exception crosses this boundary.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -86,6 +87,8 @@ void rad_destroy(rad_ctx *ctx) {
     }
   }
   cudaFree(ctx->host_slot_buf);
+  cudaFree(ctx->nu_edges_dev);
+  cudaFree(ctx->freq_buf);
   delete ctx;
 }
 
@@ -331,6 +334,11 @@ int rad::check_step_args(rad_ctx *ctx, const void *I, const rad_gas *gas, double
   if (st != RAD_OK) return st;
   if (has_halo(ctx->geom) && o->tau_const > 0.0)
     return fail(ctx, RAD_EUNSUPPORTED, "the optical-depth weighting reads the neighbour's gas: single blocks only");
+  if (ctx->n_groups > 0) {
+    if (staged) return fail(ctx, RAD_EUNSUPPORTED, "multigroup transport steps single blocks with rad_step");
+    if (o->coupling == RAD_COUPLE_THERMAL || o->rad_dom)
+      return fail(ctx, RAD_EUNSUPPORTED, "multigroup transport couples with fixed emissivity or not at all");
+  }
   if ((st = check_gas(ctx, gas, o, true)) != RAD_OK) return st;
   if (!I || !aligned16(I)) return fail(ctx, RAD_EINVAL, "I must be a 16-byte aligned device pointer");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, RAD_EINVAL, "dt must be finite and > 0");
@@ -351,7 +359,15 @@ static int ensure_scratch(rad_ctx *ctx, const rad_opts *o) {
   const rad::DevGeom &G = ctx->geom;
   size_t ncell = (size_t)G.n[0] * G.n[1] * G.n[2];
   size_t esz = o->precision == RAD_F32 ? 4 : 8;
-  size_t need = ncell * ctx->ang.n_ap * esz;
+  size_t need = ncell * ctx->ang.n_ap * esz * (size_t)std::max(1, ctx->n_groups);
+  if (ctx->n_groups > 0 && ctx->freq_bytes < need) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->freq_buf);
+    ctx->freq_buf = nullptr;
+    ctx->freq_bytes = 0;
+    if (cudaMalloc(&ctx->freq_buf, need) != cudaSuccess) return fail(ctx, RAD_ENOMEM, "frequency scratch allocation failed");
+    ctx->freq_bytes = need;
+  }
   if (ctx->scratch_I_bytes < need) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->scratch_I);
@@ -378,7 +394,10 @@ int rad_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opt
   if ((st = ensure_scratch(ctx, o)) != RAD_OK) return st;
   ctx->stage1_prec = -1;    // the scratch no longer holds a rad_step_stage stage-1 result
   std::string err;
-  st = rad::launch_step(ctx, I, gas, dt, o, gas_src, ctx->scratch_I, ctx->scratch_T, err);
+  if (ctx->n_groups > 0)
+    st = rad::launch_step_groups(ctx, I, gas, dt, o, gas_src, ctx->scratch_I, ctx->scratch_T, ctx->freq_buf, err);
+  else
+    st = rad::launch_step(ctx, I, gas, dt, o, gas_src, ctx->scratch_I, ctx->scratch_T, err);
   return st == RAD_OK ? st : fail(ctx, st, err);
 }
 
@@ -405,6 +424,39 @@ int rad_step_stage(rad_ctx *ctx, int stage, void *I, const rad_gas *gas, double 
   std::string err;
   st = rad::launch_stage_s(ctx, stage, I, gas, dt, o, gas_src, ctx->scratch_I, ctx->scratch_T, halo, err);
   return st == RAD_OK ? st : fail(ctx, st, err);
+}
+
+int rad_gas_update(rad_ctx *ctx, double *rho, double *u, double *T, const double *src, int n_src, double gamma) {
+  if (!ctx) return RAD_EINVAL;
+  if (!ctx->have_metric) return fail(ctx, RAD_ESTATE, "rad_set_metric has not been called");
+  if (!rho || !u || !T || !src) return fail(ctx, RAD_EINVAL, "null argument");
+  if (n_src < 1) return fail(ctx, RAD_EINVAL, "n_src must be >= 1");
+  if (!(gamma > 1.0) || !(gamma <= 2.0)) return fail(ctx, RAD_EINVAL, "gamma must be in (1, 2]");
+  std::string err;
+  int st = rad::launch_gas_update(ctx, rho, u, T, src, n_src, gamma, err);
+  return st == RAD_OK ? st : fail(ctx, st, err);
+}
+
+int rad_set_groups(rad_ctx *ctx, int n_groups, const double *nu_edges) {
+  if (!ctx) return RAD_EINVAL;
+  if (n_groups < 0 || n_groups > 4096 || (n_groups > 0 && !nu_edges))
+    return fail(ctx, RAD_EINVAL, "n_groups must be in 0..4096 with n_groups + 1 edges");
+  for (int g = 0; g < n_groups; ++g)
+    if (!(nu_edges[g + 1] > nu_edges[g]) || !std::isfinite(nu_edges[g]))
+      return fail(ctx, RAD_EINVAL, "edges must increase and be finite except the last");
+  if (n_groups > 0 && !(nu_edges[0] >= 0.0)) return fail(ctx, RAD_EINVAL, "the lowest edge must be >= 0");
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->nu_edges_dev);
+  ctx->nu_edges_dev = nullptr;
+  ctx->nu_edges.clear();
+  ctx->n_groups = 0;
+  if (n_groups == 0) return RAD_OK;
+  ctx->nu_edges.assign(nu_edges, nu_edges + n_groups + 1);
+  cudaError_t ce = upload(&ctx->nu_edges_dev, ctx->nu_edges, ctx->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+  if (ce != cudaSuccess) return fail(ctx, RAD_ENOMEM, std::string("group edge upload failed: ") + cudaGetErrorString(ce));
+  ctx->n_groups = n_groups;
+  return RAD_OK;
 }
 
 int rad_halo_pack(rad_ctx *ctx, const void *I, int precision, int dim, int side, void *buf) {
@@ -454,6 +506,7 @@ int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double d
   if (o->rad_dom)
     return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers the coupling at the gas velocity (rad_dom = 0)");
   if (has_halo(ctx->geom)) return fail(ctx, RAD_EUNSUPPORTED, "the adjoint steps single blocks (no RAD_BC_HALO faces)");
+  if (ctx->n_groups > 0) return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers gray transport (no groups)");
   if (!I_n || !lam_np1 || !lam_n || !g_aa || !g_as) return fail(ctx, RAD_EINVAL, "null argument");
   if (!(dt > 0.0)) return fail(ctx, RAD_EINVAL, "dt must be > 0");
   if (ctx->ang.n_ang > rad::kMaxBinsStep)

@@ -229,6 +229,10 @@ __global__ void k_geom_cols(GeomArgs A) {
       int a0 = pa[p], b0 = pb[p];
       out.K[ii][p] = (a0 == b0) ? om[ii + 1][a0][b0] : om[ii + 1][a0][b0] + om[ii + 1][b0][a0];
     }
+  for (int p = 0; p < 10; ++p) {
+    int a0 = pa[p], b0 = pb[p];
+    out.K0[p] = (a0 == b0) ? om[0][a0][b0] : om[0][a0][b0] + om[0][b0][a0];
+  }
   double lo[3] = {A.xf1[i], A.xf2[j], A.xf3[0]}, hi[3] = {A.xf1[i + 1], A.xf2[j + 1], A.xf3[1]};
   out.dV = cell_volume(A.kind, A.spin, lo, hi);
   out.invdV = 1.0 / out.dV;
@@ -303,6 +307,8 @@ __global__ void k_cols_to_f32(const ColGeo *in, ColGeoF *out, int n) {
   for (int i = 0; i < 3; ++i)
     for (int p = 0; p < 10; ++p) b.K[i][p] = (float)a.K[i][p];
   b.pad2[0] = b.pad2[1] = 0.0f;
+  for (int p = 0; p < 10; ++p) b.K0[p] = (float)a.K0[p];
+  b.pad3[0] = b.pad3[1] = 0.0f;
   out[c] = b;
 }
 

@@ -37,6 +37,7 @@ extern "C" int rad_step_host(rad_ctx *ctx, int n_items, const rad_host_item *ite
   if (!ctx->have_metric) return fail_h(ctx, RAD_ESTATE, "rad_set_metric has not been called");
   if (n_items < 0 || !o || nsteps < 1) return fail_h(ctx, RAD_EINVAL, "bad item count, options or step count");
   if (n_items == 0) return RAD_OK;
+  if (ctx->n_groups > 0) return fail_h(ctx, RAD_EUNSUPPORTED, "rad_step_host steps gray transport (no groups)");
   if (!items) return fail_h(ctx, RAD_EINVAL, "null items");
   const bool f32 = o->precision == RAD_F32;
   if (!f32 && o->precision != RAD_F64) return fail_h(ctx, RAD_EINVAL, "bad precision");

@@ -70,6 +70,7 @@ extern "C" int rad_step_noalloc(rad_ctx *ctx, void *I, const rad_gas *gas, doubl
   // the same host-side checks as rad_step, before anything is launched
   const int chk = rad::check_step_args(ctx, I, gas, dt, o);
   if (chk != RAD_OK) return chk;
+  if (ctx->n_groups > 0) return fail(ctx, RAD_EUNSUPPORTED, "rad_step_noalloc steps gray transport (no groups)");
   const rad::DevGeom &G = ctx->geom;
   const size_t ncell = (size_t)G.n[0] * G.n[1] * G.n[2];
   const size_t esz = o->precision == RAD_F32 ? 4 : 8;

@@ -57,6 +57,7 @@ struct ColGeo {
   double e[4][4];   // e[mu][A] = e^mu_A
   double K[3][10];  // omega^ihat_{AB} n^A n^B = sum_p K[i-1][p] (n n)_p, p over
                     // (00,01,02,03,11,12,13,22,23,33), off-diagonals doubled
+  double K0[10];    // the same for omega^0hat_{AB} n^A n^B (the frequency symbol n^nu = -nu K0 . (n n))
 };
 
 // Per-face geometry for the flux prefactor Delta A n^d n_0.
@@ -74,6 +75,8 @@ struct ColGeoF {
   float e[4][4];
   float K[3][10];
   float pad2[2];
+  float K0[10];
+  float pad3[2];
 };
 struct FaceGeoF {
   float ea[4];
@@ -129,6 +132,13 @@ struct rad_ctx {
   double *scratch_T = nullptr;
   size_t scratch_T_count = 0;
   int stage1_prec = -1;         // precision of the last rad_step_stage stage 1 (its result is in scratch_I)
+  // multigroup transport (rad_set_groups): 0 = gray; else the group count,
+  // the n_groups + 1 frequency edges and the per-group frequency divergence
+  int n_groups = 0;
+  std::vector<double> nu_edges;
+  double *nu_edges_dev = nullptr;
+  void *freq_buf = nullptr;
+  size_t freq_bytes = 0;
   // rad_step_adjoint scratch
   void *adj_buf = nullptr;
   size_t adj_bytes = 0;
@@ -167,6 +177,14 @@ int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_
 int launch_stage_s(rad_ctx *ctx, int stage, void *I, const rad_gas *gas, double dt, const rad_opts *opts,
                    double *gas_src, void *scratch_I, double *scratch_T, const void *const *halo,
                    std::string &err);
+// multigroup: the frequency divergence F_{g+1} - F_g of every group of I into D (frequency.cu)
+int launch_freq_div(rad_ctx *ctx, const void *I, void *D, int precision, std::string &err);
+// one RK2 step of every group (step.cu): frequency divergence, then the stage kernel per group
+int launch_step_groups(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opts *opts,
+                       double *gas_src, void *scratch_I, double *scratch_T, void *D, std::string &err);
+// rad_gas_update (gas.cu)
+int launch_gas_update(rad_ctx *ctx, double *rho, double *u, double *T, const double *src, int nsrc, double gamma,
+                      std::string &err);
 // rad_halo_pack: the kHaloLayers layers of I next to face (dim, side) into buf
 int launch_halo_pack(rad_ctx *ctx, const void *I, int precision, int dim, int side, void *buf, std::string &err);
 constexpr int kHaloLayers = 3;   // the widest stencil (PPM) reaches three cells

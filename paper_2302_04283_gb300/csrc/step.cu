@@ -14,7 +14,8 @@ namespace {
 // positive double (order preserving).
 __global__ void k_cfl(const ColGeo *cols, int n1, int n2, int ndim, const double *xf1, const double *xf2,
                       double dx3, int nang, const double *dir, const double *dOmega, const int *slot_nbr,
-                      const int *slot_edge, const double *edge_geo, int ang, unsigned long long *out) {
+                      const int *slot_edge, const double *edge_geo, int ang, const double *edges, int ngroup,
+                      unsigned long long *out) {
   int col = blockIdx.x;
   int n = threadIdx.x;
   if (n >= nang) return;
@@ -45,6 +46,20 @@ __global__ void k_cfl(const ColGeo *cols, int n1, int n2, int ndim, const double
     }
     if (rate > 0.0) best = fmin(best, dOmega[n] * n0 / rate);
   }
+  if (ngroup > 0) {
+    // multigroup: a group's donor-cell outflow through its upper edge must
+    // not empty it within the step (n^0 dnu / (nu_hi |s|))
+    const double pr[10] = {1.0, nh[1], nh[2], nh[3], nh[1] * nh[1], nh[1] * nh[2], nh[1] * nh[3],
+                           nh[2] * nh[2], nh[2] * nh[3], nh[3] * nh[3]};
+    double q0 = 0.0;
+    for (int p = 0; p < 10; ++p) q0 += cg.K0[p] * pr[p];
+    const double s = fabs(q0);
+    for (int g = 0; g < ngroup && s > 0.0; ++g) {
+      const double lo = edges[g], hi = edges[g + 1];
+      if (isinf(hi)) continue;
+      best = fmin(best, n0 * (hi - lo) / (hi * s));
+    }
+  }
   if (best < INFINITY) atomicMin(out, (unsigned long long)__double_as_longlong(best));
 }
 
@@ -69,6 +84,12 @@ cudaError_t launch_wait_selftest(rad_ctx *ctx, double seconds) {
 }
 
 cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st) {
+  bool ext = a.divF != nullptr;             // halo rows or a frequency divergence: the run-time-row kernels
+  for (int f = 0; f < 6; ++f) ext |= a.halo[f] != nullptr;
+  if (ext && !(ang && a.recon_ang != RAD_RECON_DC)) {
+    if (f32) return ang ? launch_stage_rp<float, true>(a, st) : launch_stage_rp<float, false>(a, st);
+    return ang ? launch_stage_rp<double, true>(a, st) : launch_stage_rp<double, false>(a, st);
+  }
   if (ang && a.recon_ang == RAD_RECON_PLM)
     return f32 ? launch_stage_rp<float, true, 1>(a, st) : launch_stage_rp<double, true, 1>(a, st);
   if (ang && a.recon_ang == RAD_RECON_MAPR)
@@ -160,6 +181,7 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
   a.tau_const = o->tau_const;
   a.err = ctx->err_word;
   for (int f = 0; f < 6; ++f) a.halo[f] = nullptr;
+  a.divF = nullptr;
   return a;
 }
 
@@ -235,6 +257,46 @@ int launch_stage_s(rad_ctx *ctx, int stage, void *I, const rad_gas *gas, double 
   return RAD_OK;
 }
 
+int launch_step_groups(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src,
+                       void *scratch_I, double *scratch_T, void *D, std::string &err) {
+  const bool f32 = o->precision == RAD_F32;
+  const bool ang = ctx->geom.kind != RAD_MINK_CART;
+  const DevGeom &G = ctx->geom;
+  const size_t ncell = (size_t)G.n[0] * G.n[1] * G.n[2];
+  const size_t gbytes = ncell * ctx->ang.n_ap * (f32 ? 4 : 8);      // one group's intensity array
+  auto at = [&](const void *p, int g) { return (void *)((char *)p + g * gbytes); };
+  for (int stage = 1; stage <= 2; ++stage) {
+    const void *Iin = stage == 1 ? I : scratch_I;
+    int st = launch_freq_div(ctx, Iin, D, o->precision, err);
+    if (st != RAD_OK) return st;
+    for (int g = 0; g < ctx->n_groups; ++g) {
+      rad_gas gg = *gas;
+      gg.alpha_a = gas->alpha_a ? gas->alpha_a + g * ncell : nullptr;
+      gg.alpha_s = gas->alpha_s ? gas->alpha_s + g * ncell : nullptr;
+      gg.eta = gas->eta ? gas->eta + g * ncell : nullptr;
+      StageArgs a = make_stage_args(ctx, &gg, dt, o, gas_src ? gas_src + 4 * g * ncell : nullptr);
+      if (g == 0 && stage == 1 && (st = check_stage(a, f32, err)) != RAD_OK) return st;
+      a.divF = at(D, g);
+      a.Iprev = at(Iin, g);
+      a.I0 = at(I, g);
+      a.Iout = stage == 1 ? at(scratch_I, g) : at(I, g);
+      // the gas temperature is frozen (fixed-emissivity or no coupling): every
+      // group writes the same values
+      a.T0 = gas->T;
+      a.T1 = stage == 1 ? nullptr : scratch_T;
+      a.Tout = stage == 1 ? scratch_T : gas->T;
+      a.stage2 = stage == 2;
+      a.dts = stage == 1 ? dt : 0.5 * dt;
+      const cudaError_t ce = launch_stage(a, f32, ang, ctx->stream);
+      if (ce != cudaSuccess) {
+        err = std::string("multigroup stage launch failed: ") + cudaGetErrorString(ce);
+        return RAD_ECUDA;
+      }
+    }
+  }
+  return RAD_OK;
+}
+
 int launch_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src,
                 void *scratch_I, double *scratch_T, std::string &err) {
   int st = launch_stage_s(ctx, 1, I, gas, dt, o, gas_src, scratch_I, scratch_T, nullptr, err);
@@ -256,7 +318,8 @@ int launch_cfl(rad_ctx *ctx, double cfl, double *dt_out, std::string &err) {
   int threads = (ctx->ang.n_ang + 31) / 32 * 32;
   k_cfl<<<G.n[0] * G.n[1], threads, 0, ctx->stream>>>(
       G.cols, G.n[0], G.n[1], G.ndim, xf1, xf2, dx3, ctx->ang.n_ang, ctx->dang.dir, ctx->dang.dOmega,
-      ctx->dang.slot_nbr, ctx->dang.slot_edge, ctx->dang.edge_geo, G.kind != RAD_MINK_CART, d);
+      ctx->dang.slot_nbr, ctx->dang.slot_edge, ctx->dang.edge_geo, G.kind != RAD_MINK_CART, ctx->nu_edges_dev,
+      ctx->n_groups, d);
   unsigned long long h = 0;
   cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
   cudaError_t ce = cudaStreamSynchronize(ctx->stream);

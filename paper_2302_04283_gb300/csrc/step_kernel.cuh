@@ -83,6 +83,7 @@ struct StageArgs {
   double tau_const;       // C of the optical-depth flux weighting (0: free streaming)
   int *err;
   const void *halo[6];     // ghost rows of faces shared with other blocks: face (d, side) at 2 d + side
+  const void *divF;        // multigroup: this group's frequency divergence [cell][nap] (null: gray)
 };
 
 StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad_opts *o, double *gas_src);
@@ -239,18 +240,20 @@ struct Nbr {
 // bins), 2 / 3 a ghost of a lower / upper face shared with another block
 // (RAD_BC_HALO): the value returned is then the ghost layer, 0 next to the
 // face.
+// HALO false: kernels that never see a shared face (kind is 0 or 1).
+template <bool HALO = true>
 __device__ __forceinline__ int wrap_idx(int x, int n, int bc_lo, int bc_hi, int &kind) {
   kind = 0;
   if (x < 0) {
     if (bc_lo == RAD_BC_PERIODIC) return ((x % n) + n) % n;
     if (bc_lo == RAD_BC_OUTFLOW) return 0;
-    kind = bc_lo == RAD_BC_HALO ? 2 : 1;
+    kind = (HALO && bc_lo == RAD_BC_HALO) ? 2 : 1;
     return -1 - x;
   }
   if (x >= n) {
     if (bc_hi == RAD_BC_PERIODIC) return x % n;
     if (bc_hi == RAD_BC_OUTFLOW) return n - 1;
-    if (bc_hi == RAD_BC_HALO) {
+    if (HALO && bc_hi == RAD_BC_HALO) {
       kind = 3;
       return x - n;
     }
@@ -507,6 +510,10 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   using V = typename P::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool AP = AR == 1, AM = AR == 2;
+  // the kernels with a run-time row length also read halo rows of faces
+  // shared with other blocks and add a multigroup frequency divergence; the
+  // fixed-row variants (the common grids' fast path) compile without either
+  constexpr bool EXT = NAP == 0;
   const int nap = NAP > 0 ? NAP : a.nap;                  // padded bins per row
   const int t = threadIdx.x;
   const int ncons = blockDim.x - 32;                      // consumer threads; the last warp produces
@@ -573,12 +580,12 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       }
       const int k = k0 + c;
       int ii = i, jj = j, kk = k, pol = 0;
-      if (d == 0) ii = wrap_idx(i + sg, a.n1, a.bc_lo[0], a.bc_hi[0], pol);
+      if (d == 0) ii = wrap_idx<EXT>(i + sg, a.n1, a.bc_lo[0], a.bc_hi[0], pol);
       if (d == 1) {
-        jj = wrap_idx(j + sg, a.n2, a.bc_lo[1], a.bc_hi[1], pol);
+        jj = wrap_idx<EXT>(j + sg, a.n2, a.bc_lo[1], a.bc_hi[1], pol);
         if (pol == 1 && a.n3 > 1) kk = (k + a.n3 / 2) % a.n3;
       }
-      if (d == 2) kk = wrap_idx(k + sg, a.n3, a.bc_lo[2], a.bc_hi[2], pol);
+      if (d == 2) kk = wrap_idx<EXT>(k + sg, a.n3, a.bc_lo[2], a.bc_hi[2], pol);
       const unsigned cell = (unsigned)k * ncol + col;
       const unsigned nbc = (unsigned)kk * ncol + (unsigned)jj * a.n1 + ii;
       const R uxo = (R)a.u[3 * cell], uyo = (R)a.u[3 * cell + 1], uzo = (R)a.u[3 * cell + 2];
@@ -753,15 +760,15 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   bool x1contig = true;
   for (int q = 0; q < X1N; ++q) {
     int kind = 0;
-    xs[q] = q == H ? i : wrap_idx(i + q - H, a.n1, a.bc_lo[0], a.bc_hi[0], kind);
+    xs[q] = q == H ? i : wrap_idx<EXT>(i + q - H, a.n1, a.bc_lo[0], a.bc_hi[0], kind);
     xk[q] = kind;
-    if (xs[q] != i + q - H || kind) x1contig = false;
+    if (xs[q] != i + q - H || (EXT && kind)) x1contig = false;
   }
   bool anypol = false;
   for (int q = 0; q < X2N; ++q) {
     int pol = 0;
     const int o = q < H ? q - H : q - H + 1;
-    yj[q] = a.ndim >= 2 ? wrap_idx(j + o, a.n2, a.bc_lo[1], a.bc_hi[1], pol) : j;
+    yj[q] = a.ndim >= 2 ? wrap_idx<EXT>(j + o, a.n2, a.bc_lo[1], a.bc_hi[1], pol) : j;
     ypol[q] = pol;
     anypol |= pol == 1;
   }
@@ -771,10 +778,14 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
     return base + ((size_t)kk * ncol + (size_t)jj * a.n1 + ii) * nap;
   };
   // this column's row at plane k (any k: wrapped, clamped or a halo row)
+  auto kidx = [&](int k) {
+    int kind;
+    return wrap_idx<EXT>(k, a.n3, a.bc_lo[2], a.bc_hi[2], kind);
+  };
   auto krow = [&](int k) -> const R * {
     int kind;
-    const int kk = wrap_idx(k, a.n3, a.bc_lo[2], a.bc_hi[2], kind);
-    if (kind >= 2) return halo_row<R>(a.halo, a.n1, a.n2, a.n3, 2, kind - 2, kk, i, j, 0, nap);
+    const int kk = wrap_idx<EXT>(k, a.n3, a.bc_lo[2], a.bc_hi[2], kind);
+    if (EXT && kind >= 2) return halo_row<R>(a.halo, a.n1, a.n2, a.n3, 2, kind - 2, kk, i, j, 0, nap);
     return rowp(Ip, i, j, kk);
   };
   auto produce = [&](int c, int st) {   // issue the copies of cell k0 + c into ring stage st
@@ -787,15 +798,15 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       bulk_g2s(dst, rowp(Ip, i - H, j, k), (uint32_t)(X1N * rowb), &bars[st]);
     } else {
       for (int q = 0; q < X1N; ++q) {
-        const R *src = xk[q] >= 2 ? halo_row<R>(a.halo, a.n1, a.n2, a.n3, 0, xk[q] - 2, xs[q], 0, j, k, nap)
-                                  : rowp(Ip, xs[q], j, k);
+        const R *src = (EXT && xk[q] >= 2) ? halo_row<R>(a.halo, a.n1, a.n2, a.n3, 0, xk[q] - 2, xs[q], 0, j, k, nap)
+                                           : rowp(Ip, xs[q], j, k);
         bulk_g2s(dst + q * nap, src, (uint32_t)rowb, &bars[st]);
       }
     }
     if (a.ndim >= 2) {
       for (int q = 0; q < X2N; ++q) {
         const R *src;
-        if (ypol[q] >= 2) {
+        if (EXT && ypol[q] >= 2) {
           src = halo_row<R>(a.halo, a.n1, a.n2, a.n3, 1, ypol[q] - 2, yj[q], i, 0, k, nap);
         } else {
           int kk = k;
@@ -805,7 +816,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
         bulk_g2s(dst + (SX2 + q) * nap, src, (uint32_t)rowb, &bars[st]);
       }
     }
-    if (d3) bulk_g2s(dst + SX3 * nap, krow(k + H), (uint32_t)rowb, &bars[st]);
+    if (d3) bulk_g2s(dst + SX3 * nap, EXT ? krow(k + H) : rowp(Ip, i, j, kidx(k + H)), (uint32_t)rowb, &bars[st]);
     if (ST2) bulk_g2s(dst + SI0 * nap, rowp(I0, i, j, k), (uint32_t)rowb, &bars[st]);
   };
   const int p0 = act0 ? a.perm[b0] : 0, p1 = act1 ? a.perm[b0 + 1] : 0;
@@ -851,13 +862,22 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   for (int q = 0; q < 6; ++q) pw[q] = zero;
   if (ppm && cons && d3) {
 #pragma unroll
-    for (int q = 0; q < 6; ++q) pw[q] = __ldg((const V *)(krow(k0 - 3 + q) + bb));
+    for (int q = 0; q < 6; ++q)
+      pw[q] = EXT ? __ldg((const V *)(krow(k0 - 3 + q) + bb))
+                  : __ldg((const V *)(Ip + (unsigned)kidx(k0 - 3 + q) * strideK + own));
   }
   if (!ppm && cons && d3) {
-    w0 = __ldg((const V *)(krow(k0 - 2) + bb));
-    w1 = __ldg((const V *)(krow(k0 - 1) + bb));
-    w2 = __ldg((const V *)(krow(k0) + bb));
-    w3 = __ldg((const V *)(krow(k0 + 1) + bb));
+    if (EXT) {
+      w0 = __ldg((const V *)(krow(k0 - 2) + bb));
+      w1 = __ldg((const V *)(krow(k0 - 1) + bb));
+      w2 = __ldg((const V *)(krow(k0) + bb));
+      w3 = __ldg((const V *)(krow(k0 + 1) + bb));
+    } else {
+      w0 = __ldg((const V *)(Ip + (unsigned)kidx(k0 - 2) * strideK + own));
+      w1 = __ldg((const V *)(Ip + (unsigned)kidx(k0 - 1) * strideK + own));
+      w2 = __ldg((const V *)(Ip + (unsigned)kidx(k0) * strideK + own));
+      w3 = __ldg((const V *)(Ip + (unsigned)kidx(k0 + 1) * strideK + own));
+    }
     if (plm) {
       qa = vl2<R>(w0, w1, w2);
       qb = vl2<R>(w1, w2, w3);
@@ -1041,6 +1061,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
     }
     // U* = U^{s-1} + dt L   (stage 1)   or   U^0/2 + (U^1 + dt L)/2   (stage 2), L = -(divS + divA)
     if (ANG) sx = P::add(sx, divA);
+    if (EXT && a.divF) sx = P::add(sx, __ldg((const V *)((const R *)a.divF + (unsigned)(k0 + c) * strideK + own)));
     V Us = P::fma(P::mk(-dtR, -dtR), sx, P::mul(fconv, zc));   // L = -(divS + divA)
     if (ST2) {
       const V U0 = P::mul(fconv, sv(sr + SI0 * nap));

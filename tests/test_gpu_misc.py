@@ -287,3 +287,11 @@ def test_bounded_device_wait_reports_a_timeout():
         assert e.value.status == rad.RAD_EINVAL
     finally:
         gc.close()
+
+
+def test_fp64_fma_rate_is_measured():
+    """The measured FP64 FMA rate (the FP64 kernels' roofline denominator) is
+    a positive rate of the order GB300's FP64 units give (nominal 1.25
+    TFLOP/s), not a placeholder."""
+    r = rad.rad_fp64_fma_rate(1.0)
+    assert 0.1 < r < 100.0, r
