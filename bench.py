@@ -11,9 +11,14 @@ synthetic fields.  The metric is cell-angle updates per second.
 
 --impl reference times the FP64 CPU oracle on this host's cores on a bounded
 sample of the same workload (the comparison arm; it is a deliberately plain
-program).  With N > 1 (torchrun) every rank runs an independent replica of
-the workload on its own GPU (no halo exchange is built), and value is the
-sum over ranks.
+program).  With N > 1 (torchrun) the domain is N copies of the workload's
+periodic 128^3 block laid along x1, one block per GPU: before each RK stage
+every rank packs the three cell layers next to its two x1 faces, exchanges
+them with its neighbours over NCCL and steps on the received halos (weak
+scaling; value is the whole job's cell-angle updates over the slowest
+rank's time).  --replicas runs N unconnected copies instead; --decomp-self
+runs the one-GPU case through the same pack / exchange / staged path, the
+block's x1 faces shared with itself.
 """
 import argparse
 import hashlib
@@ -53,6 +58,9 @@ def parse():
     p.add_argument("--n", type=int, default=None, help="cells per side (default: the workload's 128)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the FP64-path, accuracy and adjoint/forward measurements")
+    p.add_argument("--replicas", action="store_true", help="N > 1: unconnected replicas instead of blocks")
+    p.add_argument("--decomp-self", action="store_true",
+                   help="N = 1: step through the block path, x1 faces shared with the block itself")
     return p.parse_args()
 
 
@@ -142,14 +150,22 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def setup_gpu(prec, dev, n=None, name=WORKLOAD):
+def setup_gpu(prec, dev, n=None, name=WORKLOAD, block=None):
+    """block = (index, count): the block's x1 faces are shared with its
+    neighbours along x1 (RAD_BC_HALO) and its x1 coordinates are shifted by
+    `index` periods."""
     import torch
     import paper_2302_04283_gb300 as rad
     import workloads as W
     w = W.make(name, n=(n, n, n) if n else None, with_intensity=False)
     ctx = rad.rad_create(torch.cuda.current_stream())
     na, nap = rad.rad_init_angles(ctx, w["level"])
-    rad.rad_set_metric(ctx, w["kind"], w["spin"], w["ndim"], w["xf"], w["bc"])
+    xf, bc = w["xf"], w["bc"]
+    if block is not None:
+        period = float(xf[0][-1] - xf[0][0])
+        xf = [xf[0] + block[0] * period, xf[1], xf[2]]
+        bc = (("halo", "halo"), bc[1], bc[2])
+    rad.rad_set_metric(ctx, w["kind"], w["spin"], w["ndim"], xf, bc)
     dt = rad.rad_cfl_dt(ctx, w["cfl"])
     sh = (w["n"][2], w["n"][1], w["n"][0])
     tdt = torch.float32 if prec == "f32" else torch.float64
@@ -202,11 +218,35 @@ def profiled_traffic(precision, ncell):
         return None
 
 
+def block_step_fn(rad, ctx, I, gas, dt, opts, src, rank, world, nap, tdt, dev, sh):
+    """One RK2 step of this rank's block: x1 halos exchanged with the
+    neighbouring ranks over torch.distributed (NCCL), or, for one block
+    whose faces are shared with itself, copied locally."""
+    from paper_2302_04283_gb300 import blocks as B
+    nb = {(0, 0): (rank - 1) % world, (0, 1): (rank + 1) % world}
+    send, recv = B.halo_buffers(sh, nb, nap, tdt, dev)
+    move = None
+    if world == 1:
+        def move(s_, r_):
+            r_[(0, 0)].copy_(s_[(0, 1)])
+            r_[(0, 1)].copy_(s_[(0, 0)])
+
+    def step():
+        B.step_block(rad, ctx, I, gas, dt, opts, src, nb, send, recv, move)
+    return step
+
+
 def run_ours(args, rank, world):
     import torch
     dev = f"cuda:{int(os.environ.get('LOCAL_RANK', 0))}"
     torch.cuda.set_device(dev)
-    rad, w, ctx, na, nap, dt, sh, tdt, I, gas = setup_gpu(args.precision, dev, args.n)
+    blocks = (world > 1 and not args.replicas) or (world == 1 and args.decomp_self)
+    rad, w, ctx, na, nap, dt, sh, tdt, I, gas = setup_gpu(args.precision, dev, args.n,
+                                                          block=(rank, world) if blocks else None)
+    if blocks and world > 1:
+        dt_t = torch.tensor([dt], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(dt_t, op=torch.distributed.ReduceOp.MIN)     # the domain's bound
+        dt = float(dt_t.item())
     ncell = sh[0] * sh[1] * sh[2]
     esz = 4 if args.precision == "f32" else 8
     prec = rad.RAD_F32 if args.precision == "f32" else rad.RAD_F64
@@ -218,10 +258,13 @@ def run_ours(args, rank, world):
     T0 = gas["T"].clone()
     st = torch.cuda.current_stream()
 
+    advance = (block_step_fn(rad, ctx, I, gas, dt, opts, src, rank, world, nap, tdt, dev, sh) if blocks
+               else (lambda: rad.rad_step(ctx, I, gas, dt, opts, src)))
+
     def step(ev=None):
         if ev:
             ev[0].record(st)
-        rad.rad_step(ctx, I, gas, dt, opts, src)
+        advance()
         if ev:
             ev[1].record(st)
         rad.rad_moments(ctx, I, prec, rad.RAD_FRAME_TETRAD, mom, gas, R)
@@ -293,16 +336,21 @@ def run_ours(args, rank, world):
                    "cells": ncell, "bins": na, "precision": args.precision,
                    "moments": "split-bf16 tensor cores" if mom == rad.RAD_MOM_BF16X3 else "CUDA cores",
                    "l2": "inputs larger than L2 (I is %.2f GB), no flush" % (ncell * nap * esz / 1e9),
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": (f"x1 blocks x{world}, 128^3 cells per GPU, ghost exchange before each stage "
+                                   f"({'NCCL' if world > 1 else 'the block with itself'})") if blocks
+                                  else f"replicas x{world}"},
         "roofline": roof,
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": (7 if blocks else 3) * args.steps,
         "clocks": clk.summary(),
         "breakdown_ms_per_step": {"rad_step": stage_ms / args.steps, "rad_moments": mom_ms / args.steps,
                                   "step_min": min(step_ms), "step_median": sorted(step_ms)[len(step_ms) // 2],
                                   "step_max": max(step_ms)},
     }
     if not args.no_e2e:
-        res["e2e"] = run_e2e(args, rad, ctx, dt, opts, prec, mom, sh, na, nap, tdt, dev, world)
+        if blocks:
+            res["e2e"] = run_e2e_blocks(args, rad, ctx, dt, opts, prec, mom, sh, na, nap, tdt, dev, world, rank)
+        else:
+            res["e2e"] = run_e2e(args, rad, ctx, dt, opts, prec, mom, sh, na, nap, tdt, dev, world)
     rad.rad_destroy(ctx)
     if not args.no_extras and rank == 0 and args.precision == "f32":
         res["extras"] = run_extras(args, dev)
@@ -497,6 +545,59 @@ def run_e2e(args, rad, ctx, dt, opts, prec, mom, sh, na, nap, tdt, dev, world):
                           "intensity stays on the device (rad_host_item.I_out is null)"}
 
 
+def run_e2e_blocks(args, rad, ctx, dt, opts, prec, mom, sh, na, nap, tdt, dev, world, rank):
+    """End to end for the block path: every step copies this rank's block
+    (I and the gas state) from pinned host memory, steps it with the ghost
+    exchange, contracts the moments and reads the moments and temperature
+    back (one stream, no overlap)."""
+    import torch
+    import workloads as W
+    w = W.make(WORKLOAD, n=(sh[2], sh[1], sh[0]), with_intensity=False)
+    hI = torch.empty(sh + (nap,), dtype=tdt, pin_memory=True)
+    g = torch.Generator()
+    g.manual_seed(w["seed"])
+    T = torch.tensor(w["T"])
+    hI[..., :na] = ((T ** 4 / (4 * math.pi))[..., None] *
+                    (1 + 0.1 * (2 * torch.rand(sh + (na,), generator=g, dtype=torch.float64) - 1))).to(tdt)
+    hI[..., na:] = 0
+    hgas = {k: torch.tensor(np.ascontiguousarray(w[k])).pin_memory() for k in ("rho", "u", "alpha_a", "alpha_s", "T")}
+    hR = torch.empty(sh + (10,), dtype=tdt, pin_memory=True)
+    hT = torch.empty(sh, dtype=torch.float64, pin_memory=True)
+    dI = torch.empty(sh + (nap,), dtype=tdt, device=dev)
+    dgas = {k: torch.empty_like(v, device=dev) for k, v in hgas.items()}
+    dgas["eta"] = None
+    dR = torch.empty(sh + (10,), dtype=tdt, device=dev)
+    src = torch.zeros(sh + (4,), dtype=torch.float64, device=dev)
+    step = block_step_fn(rad, ctx, dI, dgas, dt, opts, src, rank, world, nap, tdt, dev, sh)
+
+    def one():
+        dI.copy_(hI, non_blocking=True)
+        for k, v in hgas.items():
+            dgas[k].copy_(v, non_blocking=True)
+        step()
+        rad.rad_moments(ctx, dI, prec, rad.RAD_FRAME_TETRAD, mom, dgas, dR)
+        hR.copy_(dR, non_blocking=True)
+        hT.copy_(dgas["T"], non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        one()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    rate = job_rate(sh[0] * sh[1] * sh[2] * na * args.steps, el, dev, world)
+    h2d = hI.numel() * hI.element_size() + sum(v.numel() * v.element_size() for v in hgas.values())
+    d2h = hR.numel() * hR.element_size() + hT.numel() * hT.element_size()
+    return {"value": rate, "unit": "cell-angle updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "api": "blocks.step_block (rad_halo_pack, exchange, rad_step_stage) + rad_moments, host buffers "
+                   "copied in and out every step on one stream",
+            "reads_back": "moments R^{AB} [cell][10] and gas temperature T [cell] of this rank's block"}
+
+
 # ------------------------------------------------------- oracle on CPU
 class OracleSample:
     """The FP64 oracle on a bounded sample of the workload: the same recipe on
@@ -574,8 +675,12 @@ def main():
             print(json.dumps(run_reference(args)), flush=True)
         return
     if world > 1:
+        import datetime
         import torch
-        torch.distributed.init_process_group("nccl")
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        # a bounded timeout: a rank that stops answering ends the job with an
+        # error instead of holding every GPU
+        torch.distributed.init_process_group("nccl", timeout=datetime.timedelta(seconds=300))
     res = run_ours(args, rank, world)
     if rank == 0:
         if not args.no_cpu_baseline:

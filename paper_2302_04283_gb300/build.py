@@ -14,7 +14,7 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
 
 SOURCES = ["angles.cpp", "capi.cu", "geom.cu", "step.cu",
-           "stage_f32_flat.cu", "stage_f32_flat164.cu", "stage_f32_ang.cu", "stage_f32_ang164.cu",
+           "stage_f32_flat.cu", "stage_f32_flat164.cu", "stage_f32_flat164x.cu", "stage_f32_ang.cu", "stage_f32_ang164.cu",
            "stage_f32_ang364.cu", "stage_f32_ang644.cu", "stage_f32_angplm.cu", "stage_f32_angmapr.cu",
            "stage_f64_flat.cu", "stage_f64_ang.cu", "stage_f64_angplm.cu", "stage_f64_angmapr.cu",
            "moments.cu", "moments_tc.cu", "adjoint.cu", "adjoint_tadj_f32_flat.cu", "adjoint_tadj_f32_ang.cu",

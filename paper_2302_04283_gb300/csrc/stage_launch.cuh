@@ -36,7 +36,7 @@ cudaError_t launch_stage_pt(const StageArgs &a, int threads, dim3 grid, cudaStre
 
 template <typename R, bool ANG, int AR, int NAP>
 cudaError_t launch_stage_rp(const StageArgs &a, cudaStream_t st) {
-  if (NAP > 0 && a.nap != NAP) return cudaErrorInvalidValue;
+  if (NAP != 0 && a.nap != (NAP > 0 ? NAP : -NAP)) return cudaErrorInvalidValue;
   const int threads = (a.nap / 2 + 31) / 32 * 32;     // two bins per consumer thread
   const int nchunk = (a.n3 + a.kc - 1) / a.kc;
   const dim3 grid((unsigned)((long long)a.n1 * a.n2 * nchunk));

@@ -87,6 +87,7 @@ cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st
   bool ext = a.divF != nullptr;             // halo rows or a frequency divergence: the run-time-row kernels
   for (int f = 0; f < 6; ++f) ext |= a.halo[f] != nullptr;
   if (ext && !(ang && a.recon_ang != RAD_RECON_DC)) {
+    if (f32 && !ang && a.nap == kNapGeo4) return launch_stage_rp<float, false, 0, -kNapGeo4>(a, st);
     if (f32) return ang ? launch_stage_rp<float, true>(a, st) : launch_stage_rp<float, false>(a, st);
     return ang ? launch_stage_rp<double, true>(a, st) : launch_stage_rp<double, false>(a, st);
   }

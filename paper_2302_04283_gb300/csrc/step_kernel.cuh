@@ -91,7 +91,8 @@ cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st
 // One precision / geometry class of stage launches (explicitly instantiated in
 // stage_<precision>_<flat|ang>.cu, one translation unit each).
 // NAP > 0 fixes the padded row length (a.nap) at compile time; 0 reads it
-// from the arguments.
+// from the arguments; NAP < 0 fixes it at -NAP in a kernel that also reads
+// halo rows and a frequency divergence (those, like NAP = 0, do).
 // AR: angular reconstruction (curved space): 0 donor cell, 1 PLM along the
 // lines of a latitude-longitude grid, 2 minimum-angle planes on a geodesic grid.
 template <typename R, bool ANG, int AR = 0, int NAP = 0>
@@ -498,7 +499,8 @@ __host__ __device__ constexpr size_t stage_smem(int threads, int nap, int kc, in
 template <typename R, bool ANG, int RC, bool ST2, bool TAU, int AR = 0, int NAP = 0>
 // AR: angular reconstruction, 0 donor cell, 1 PLM along the lines of a
 // latitude-longitude grid, 2 minimum-angle planes (MAPR) on a geodesic grid.
-// NAP: the padded row length when fixed at compile time (0: a.nap).
+// NAP: the padded row length when fixed at compile time (0: a.nap; < 0: -NAP,
+// with the halo and frequency terms).
 // Register budget: the flat FP32 DC / PLM kernels are held to 96 registers
 // (the bound of a 544-thread block) so that five 128-thread CTAs fit an SM;
 // the others get 128 (the curved kernels' CTAs are limited by shared memory
@@ -513,8 +515,10 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   // the kernels with a run-time row length also read halo rows of faces
   // shared with other blocks and add a multigroup frequency divergence; the
   // fixed-row variants (the common grids' fast path) compile without either
-  constexpr bool EXT = NAP == 0;
-  const int nap = NAP > 0 ? NAP : a.nap;                  // padded bins per row
+  // (a negative NAP is the fixed row length -NAP with both: the level-4
+  // flat kernel of the block path)
+  constexpr bool EXT = NAP <= 0;
+  const int nap = NAP > 0 ? NAP : (NAP < 0 ? -NAP : a.nap);   // padded bins per row
   const int t = threadIdx.x;
   const int ncons = blockDim.x - 32;                      // consumer threads; the last warp produces
   const bool cons = t < ncons;

@@ -9,14 +9,16 @@ random velocities <= 0.3c, alpha_s = alpha_a / 2, thermal coupling, PLM,
 the n0crit guard, dt = 0.3 x the oracle's time-step bound.
 
 The oracle advances the window of the subvolume plus `margin` cells on every
-side (cut with outflow boundaries: wrong values at the cut travel inward by
-at most the numerical domain of dependence, far less than the margin at
-these Courant numbers); it does so for two margins and records their
-largest difference over the subvolume, which bounds the truncation error.
+side (cut with outflow boundaries: wrong values at the cut travel inward
+within the numerical domain of dependence, two cells per RK stage with
+weights that fall with the Courant number); it does so for two margins and
+records their largest difference over the subvolume, which bounds the
+truncation error (margins of 8 and 12 cells still differed by 4e-11
+relative; 12 and 16 are used).
 The time step is the oracle's bound over every (r, theta) column (the
 metric does not depend on phi, so one phi slab gives the full grid's bound).
 
-    python tests/golden/make_torus3d_big_subvolume.py [--margins 8 12]
+    python tests/golden/make_torus3d_big_subvolume.py [--margins 12 16]
 
 writes tests/golden/torus3d_big_subvolume.npz: R (tetrad-frame moments
 [24, 24, 24, 10]), T [24, 24, 24], src (gas source of the last step
@@ -91,7 +93,7 @@ def run(w, ang, origin, margin, dt):
 
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("--margins", type=int, nargs=2, default=[8, 12])
+    p.add_argument("--margins", type=int, nargs=2, default=[12, 16])
     p.add_argument("--out", default=os.path.join(HERE, "torus3d_big_subvolume.npz"))
     a = p.parse_args()
     w = W.make("torus3d_big", with_intensity=False)
@@ -106,7 +108,7 @@ def main():
     (I, T, src), (I2, T2, src2) = res
     diff = max(float((I - I2).abs().max() / I2.abs().max()), float((T - T2).abs().max() / T2.abs().max()))
     print("margin difference (relative)", diff, flush=True)
-    assert diff < 1e-14, diff
+    assert diff < 1e-13, diff
     R = OM.moments(I2, ang)
     rng = np.random.default_rng(20)
     cells = rng.integers(0, SUB, (NSAMPLE, 3))
