@@ -391,8 +391,10 @@ int rad_step_host(rad_ctx *ctx, int n_items, const rad_host_item *items, double 
  * optical-depth weighting of Sec. 2.4) the opacity gradients include the
  * path through the face weights.  Any spatial reconstruction (DC, PLM, PPM)
  * and any angular one (DC, line PLM, MAPR), the limiters and the plane choice
- * differentiated on their active branches; rad_dom must be 0
- * (RAD_EUNSUPPORTED otherwise).  lam arrays use the intensity
+ * differentiated on their active branches.  With rad_dom = 1 the gradient
+ * also runs through the substituted velocity (the radiation velocity, the
+ * momentum fractions on their unclamped range, the trigger held fixed) into
+ * the intensities, the temperature and the opacities.  lam arrays use the intensity
  * layout and precision; lamT arrays are device FP64 [k][j][i].  lamT_np1 may
  * be NULL (zero), lamT_n may be NULL (not written) and may equal lamT_np1;
  * g_eta may be NULL.

@@ -231,8 +231,27 @@ __global__ void __launch_bounds__(MAXT) k_couple_adj(AdjArgs A) {
       const double lc1 = Isd * lpd + Isd * wbd * lD;
       const double lIs = c1d * lpd + cm1d * wbd * lD + wbd * lEm;
       const double lrden = n0d * lc1 + c2pd / (nbd * nbd * nbd) * S * lpd + dOd / nbd * lA2s;
+      // with the radiation-dominated substitution the velocity is itself a
+      // function of the intensities: dL/du through every n^0bar = u^0 - u.n
+      double dudn[3] = {0.0, 0.0, 0.0};
+      if (A.lam_u && act) {
+        const double inb = 1.0 / nbd;
+        const double drden = -(aad + asd) * dtsd * rdend * rdend;
+        const double dLdnb = lrden * drden - 3.0 * c2pd * rdend * inb * inb * inb * inb * S * lpd +
+                             (cm1d * Isd * lD + Isd * lEm) * 2.0 * nbd * dOd - lA2s * dOd * rdend * inb * inb;
+        const double u0d = sqrt(1.0 + uxd * uxd + uyd * uyd + uzd * uzd);
+        dudn[0] = dLdnb * (uxd / u0d - xh);
+        dudn[1] = dLdnb * (uyd / u0d - yh);
+        dudn[2] = dLdnb * (uzd / u0d - zh);
+      }
       double t2[4];
-      cta_sum4<double>(act ? -nbd * dtsd * rdend * rdend * lrden : 0.0, 0.0, 0.0, 0.0, dbuf, nwarp, lane, warp, t2);
+      cta_sum4<double>(act ? -nbd * dtsd * rdend * rdend * lrden : 0.0, dudn[0], dudn[1], dudn[2], dbuf, nwarp,
+                       lane, warp, t2);
+      if (n == 0 && A.lam_u) {
+        A.lam_u[3 * cell] = t2[1];
+        A.lam_u[3 * cell + 1] = t2[2];
+        A.lam_u[3 * cell + 2] = t2[3];
+      }
       if (n == 0) {
         const double laE = t2[0];
         A.g_aa[cell] += sc[4] + laE;
@@ -307,7 +326,7 @@ int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
   const size_t esz = f32 ? 4 : 8;
   const size_t ib = (ncell * ctx->ang.n_ap * esz + 255) / 256 * 256;
   const size_t tb = (ncell * sizeof(double) + 255) / 256 * 256;
-  const size_t need = 5 * ib + 6 * tb;
+  const size_t need = 5 * ib + 12 * tb;
   if (ctx->adj_bytes < need) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->adj_buf);
@@ -324,6 +343,9 @@ int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
   double *T1 = (double *)(p + 5 * ib), *T2 = (double *)(p + 5 * ib + tb);
   double *lamT1 = (double *)(p + 5 * ib + 2 * tb);   // adjoint of the stage-1 temperature
   double *gtau = (double *)(p + 5 * ib + 3 * tb);    // [cell][3] lower-face sums (optical-depth weighting)
+  double *usub = (double *)(p + 5 * ib + 6 * tb);    // [cell][3] substituted velocity (rad_dom)
+  double *lamu = (double *)(p + 5 * ib + 9 * tb);    // [cell][3] dL/du of the substituted velocity (rad_dom)
+  const bool rd = o->rad_dom != 0;
   const bool thermal = o->coupling == RAD_COUPLE_THERMAL;
   if (!thermal && lamT_n && lamT_n != lamT_np1) {
     // the temperature passes through an uncoupled or fixed-emissivity step
@@ -350,7 +372,11 @@ int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
   s.Tout = T1;
   s.stage2 = 0;
   s.dts = dt;
+  // with the radiation-dominated substitution the forward stage is the
+  // transport-only stage kernel followed by the substituted coupling
+  if (rd) s.mode = RAD_COUPLE_NONE;
   cudaError_t ce = launch_stage(s, f32, ang, ctx->stream);
+  if (ce == cudaSuccess && rd) ce = launch_couple_rd(s, f32, T1, T1, ctx->stream);
   if (ce == cudaSuccess) {
     s.Iprev = I1;
     s.I0 = I_n;
@@ -364,6 +390,7 @@ int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
     ce = launch_stage(s, f32, ang, ctx->stream);
   }
   s.Istar = nullptr;
+  s.mode = o->coupling;
   // ---- stage 2 backwards
   AdjArgs A;
   A.s = s;
@@ -382,13 +409,35 @@ int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
   A.accTa = 0;
   A.outTb = lamT1;
   A.wTb = 0.5;
+  A.lam_u = nullptr;
+  // the coupling adjoint of one stage; with rad_dom the coupling ran at the
+  // substituted velocity: recompute it, take the coupling back at it (which
+  // also gives dL/du), then take dL/du back through the substitution
+  auto couple_adj = [&](const void *Istar, const double *Tm) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    if (rd) {
+      e = launch_rd_sub(0, A.s, f32, Istar, Tm, usub, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, nullptr,
+                        0.0, ctx->stream);
+      A.s.u = usub;
+      A.lam_u = lamu;
+    }
+    if (e == cudaSuccess) e = f32 ? launch_couple_adj<float>(A, ctx->stream) : launch_couple_adj<double>(A, ctx->stream);
+    if (rd) {
+      A.s.u = gas->u;
+      A.lam_u = nullptr;
+      if (e == cudaSuccess)
+        e = launch_rd_sub(1, A.s, f32, Istar, Tm, nullptr, lamu, A.mu, g_aa, g_as, A.outTa, A.wTa, A.outTb, A.wTb,
+                          ctx->stream);
+    }
+    return e;
+  };
   if (ce == cudaSuccess) {
     A.s.dts = 0.5 * dt;
     A.s.stage2 = 1;
     A.lam = lam_np1;
     A.Istar = I2s;
     A.mu = mu;
-    ce = f32 ? launch_couple_adj<float>(A, ctx->stream) : launch_couple_adj<double>(A, ctx->stream);
+    ce = couple_adj(I2s, T2);     // T2 holds the stage's T- = (T^0 + T^1) / 2
   }
   if (ce == cudaSuccess) {
     A.Ilin = I1;
@@ -413,7 +462,7 @@ int launch_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double dt,
     A.lam = lamI1;
     A.Istar = I1s;
     A.mu = mu;
-    ce = f32 ? launch_couple_adj<float>(A, ctx->stream) : launch_couple_adj<double>(A, ctx->stream);
+    ce = couple_adj(I1s, gas->T);
   }
   if (ce == cudaSuccess) {
     A.Ilin = I_n;

@@ -35,6 +35,9 @@ struct AdjArgs {
   // cell's lower face of dL/df * df/d(face alpha_E) (written by
   // k_transport_adj, read by k_tau_grad)
   double *gtau;
+  // radiation-dominated substitution: the coupling runs at the substituted
+  // velocity (s.u points at it) and writes dL/du [cell][3] here (nullable)
+  double *lam_u;
 };
 
 // Three-value CTA reduction used per cell: warp reduce-scatter, then every

@@ -503,8 +503,6 @@ int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double d
   int st = check_opts(ctx, o);
   if (st != RAD_OK) return st;
   if ((st = check_gas(ctx, gas, o, true)) != RAD_OK) return st;
-  if (o->rad_dom)
-    return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers the coupling at the gas velocity (rad_dom = 0)");
   if (has_halo(ctx->geom)) return fail(ctx, RAD_EUNSUPPORTED, "the adjoint steps single blocks (no RAD_BC_HALO faces)");
   if (ctx->n_groups > 0) return fail(ctx, RAD_EUNSUPPORTED, "the adjoint covers gray transport (no groups)");
   if (!I_n || !lam_np1 || !lam_n || !g_aa || !g_as) return fail(ctx, RAD_EINVAL, "null argument");

@@ -190,7 +190,236 @@ __global__ void __launch_bounds__(1024) k_couple_rd(RdArgs a) {
   }
 }
 
+// The substitution alone, for the adjoint: mode 0 writes the substituted
+// velocity of every cell (usub [cell][3]) from the saved pre-coupling
+// intensities I*; mode 1 takes dL/du_sub (lam_u) back to the intensities
+// (added to mu = dL/dU*, i.e. divided by n^0 n_0, zero in guarded bins), to
+// the stage's T- (added to outTa / outTb with weights wTa / wTb) and to
+// dL/dalpha_a, dL/dalpha_s.  The chain, per cell and component a where the
+// substitution is active:
+//   u^a = (1 - f^a) u_gas^a + f^a u_rad^a,  f^a = clamp(G^a dt / gap^a, 0, 1)
+//   (differentiated where 0 < G^a dt / gap^a < 1),
+//   gap^a = w (gamma^2 v^a - u_gas^0 u_gas^a),  u_rad^a = gamma v^a,
+//   v^a = R^{0a} / R^{00},  w = rho + Gamma c_v T-,
+//   G^a = -(alpha_a a T-^4 + alpha_s Ebar_gas) u_gas^a - alpha_E u_b R^{ab},
+// and Ebar_gas, R^{AB} are sums of I* over the bins.  FP64 throughout.
+struct RdAdjArgs {
+  int mode;
+  const void *Istar;            // working precision R
+  void *mu;                     // mode 1: dL/dU* (+=)
+  const double *Tm;             // T- of the stage
+  const double *rho, *u, *aa, *as;
+  double *usub;                 // mode 0 output
+  const double *lam_u;          // mode 1 input
+  double *g_aa, *g_as;
+  double *outTa, *outTb;
+  double wTa, wTb;
+  double dts;
+  int n1, n2, n3, nap, nang, kc;
+  const ColGeo *cols64;
+  const void *colsR;
+  const double *dir, *dOmega;
+  int zero_guard;
+  double n0crit, a_rad, gamma, inv_gm1;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(1024) k_rd_sub(RdAdjArgs a) {
+  using Col = typename GeoTypes<R>::Col;
+  __shared__ double buf[32 * 11];
+  __shared__ double sc[11];
+  const int n = threadIdx.x;
+  const int nwarp = blockDim.x >> 5, lane = n & 31, warp = n >> 5;
+  const bool act = n < a.nang;
+  const int nchunk = (a.n3 + a.kc - 1) / a.kc;
+  const int col = blockIdx.x / nchunk, chunk = blockIdx.x % nchunk;
+  const int k0 = chunk * a.kc, nc = min(a.kc, a.n3 - k0);
+  const unsigned ncol = (unsigned)a.n1 * a.n2;
+  const Col &cr = ((const Col *)a.colsR)[col];
+  double xh = 0.0, yh = 0.0, zh = 0.0, dO = 0.0;
+  R inv_f = R(0);
+  if (act) {
+    xh = a.dir[3 * n];
+    yh = a.dir[3 * n + 1];
+    zh = a.dir[3 * n + 2];
+    dO = a.dOmega[n];
+    // the guard decision and U -> I factor exactly as the stage kernel takes them
+    const R nl = fma((R)zh, cr.M[0][3], fma((R)yh, cr.M[0][2], fma((R)xh, cr.M[0][1], cr.M[0][0])));
+    const bool keep = !(a.zero_guard && fabs((double)nl) < a.n0crit);
+    inv_f = keep ? R(1) / (cr.n0up * nl) : R(0);
+  }
+  const R *Is_ = (const R *)a.Istar;
+  R *mu = (R *)a.mu;
+  for (int c = 0; c < nc; ++c) {
+    const unsigned cell = (unsigned)(k0 + c) * ncol + col;
+    const size_t e = (size_t)cell * a.nap + (act ? n : 0);
+    const double Is = act ? (double)Is_[e] : 0.0;
+    const double ux = a.u[3 * cell], uy = a.u[3 * cell + 1], uz = a.u[3 * cell + 2];
+    const double u0 = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+    const double nbg = u0 - (ux * xh + uy * yh + uz * zh);
+    {
+      const double w = Is * dO;
+      double v[11] = {w * nbg * nbg, w, w * xh, w * yh, w * zh, w * xh * xh, w * xh * yh, w * xh * zh,
+                      w * yh * yh, w * yh * zh, w * zh * zh};
+      block_sum<11>(v, buf, nwarp, lane, warp);
+      if (n == 0) {
+        const double Em = v[0], R00 = v[1];
+        const double R0[3] = {v[2], v[3], v[4]};
+        const double Rab[3][3] = {{v[5], v[6], v[7]}, {v[6], v[8], v[9]}, {v[7], v[9], v[10]}};
+        const double rho = a.rho[cell], Tm = a.Tm[cell];
+        const double cv = rho * a.inv_gm1, ugas = cv * Tm;
+        const double ug[3] = {ux, uy, uz};
+        double us[3] = {ux, uy, uz};
+        bool active = Em > rho + ugas && R00 > 0.0;
+        double vr[3] = {0.0, 0.0, 0.0}, v2 = 0.0;
+        if (active) {
+          for (int i = 0; i < 3; ++i) {
+            vr[i] = R0[i] / R00;
+            v2 += vr[i] * vr[i];
+          }
+          active = v2 < 1.0;
+        }
+        // mode 1 results: dL/dEbar_gas, dL/dR^{00}, dL/dR^{0a}, dL/dR^{ab}
+        // (ordered pairs), dL/dT-, dL/dalpha_a, dL/dalpha_s
+        double lEm = 0.0, lR00 = 0.0, lR0[3] = {0.0, 0.0, 0.0}, lRab[3][3] = {{0.0}};
+        double lT = 0.0, laa = 0.0, las = 0.0;
+        if (active) {
+          const double gr = 1.0 / sqrt(1.0 - v2);
+          const double w = rho + ugas + (a.gamma - 1.0) * ugas;
+          const double aa = a.aa[cell], as = a.as[cell], aE = aa + as;
+          const double T2 = Tm * Tm;
+          const double emit = aa * a.a_rad * T2 * T2 + as * Em;
+          double urad[3], uR[3], G[3], gap[3], f[3];
+          bool interior[3];
+          for (int i = 0; i < 3; ++i) {
+            urad[i] = gr * vr[i];
+            uR[i] = -u0 * R0[i] + ug[0] * Rab[i][0] + ug[1] * Rab[i][1] + ug[2] * Rab[i][2];
+            G[i] = -emit * ug[i] - aE * uR[i];
+            gap[i] = w * gr * urad[i] - w * u0 * ug[i];
+            const double fr = gap[i] != 0.0 ? G[i] * a.dts / gap[i] : 0.0;
+            interior[i] = gap[i] != 0.0 && fr > 0.0 && fr < 1.0;
+            f[i] = fmin(fmax(fr, 0.0), 1.0);
+            us[i] = (1.0 - f[i]) * ug[i] + f[i] * urad[i];
+          }
+          if (a.mode == 1) {
+            double lurad[3], lgap[3], lw = 0.0, lemit = 0.0;
+            for (int i = 0; i < 3; ++i) {
+              const double lu = a.lam_u[3 * cell + i];
+              const double lf = lu * (urad[i] - ug[i]);
+              lurad[i] = lu * f[i];
+              double lG = 0.0;
+              lgap[i] = 0.0;
+              if (interior[i]) {
+                lG = lf * a.dts / gap[i];
+                lgap[i] = -lf * f[i] / gap[i];
+              }
+              lw += lgap[i] * (gr * urad[i] - u0 * ug[i]);
+              lemit -= lG * ug[i];
+              const double luR = -aE * lG;
+              laa -= lG * uR[i];
+              las -= lG * uR[i];
+              lR0[i] -= u0 * luR;
+              for (int b = 0; b < 3; ++b) lRab[i][b] += ug[b] * luR;
+            }
+            laa += lemit * a.a_rad * T2 * T2;
+            las += lemit * Em;
+            lT += lemit * aa * a.a_rad * 4.0 * T2 * Tm;
+            lEm += lemit * as;
+            lT += lw * a.gamma * cv;
+            // v -> (u_rad = gamma v, gap through w gamma^2 v)
+            double lv[3];
+            for (int b = 0; b < 3; ++b) {
+              double s = 0.0;
+              for (int i = 0; i < 3; ++i) {
+                const double dd = i == b ? 1.0 : 0.0;
+                s += lurad[i] * (gr * dd + gr * gr * gr * vr[i] * vr[b]) +
+                     w * lgap[i] * (gr * gr * dd + 2.0 * gr * gr * gr * gr * vr[i] * vr[b]);
+              }
+              lv[b] = s;
+            }
+            for (int i = 0; i < 3; ++i) {
+              lR0[i] += lv[i] / R00;
+              lR00 -= lv[i] * vr[i] / R00;
+            }
+          }
+        }
+        if (a.mode == 0) {
+          a.usub[3 * cell] = us[0];
+          a.usub[3 * cell + 1] = us[1];
+          a.usub[3 * cell + 2] = us[2];
+        } else {
+          a.g_aa[cell] += laa;
+          a.g_as[cell] += las;
+          if (a.outTa) a.outTa[cell] += a.wTa * lT;
+          if (a.outTb) a.outTb[cell] += a.wTb * lT;
+          sc[0] = lEm;
+          sc[1] = lR00;
+          for (int i = 0; i < 3; ++i) sc[2 + i] = lR0[i];
+          // symmetric dL/dR^{ab} per unordered pair (11 12 13 22 23 33)
+          sc[5] = lRab[0][0];
+          sc[6] = lRab[0][1] + lRab[1][0];
+          sc[7] = lRab[0][2] + lRab[2][0];
+          sc[8] = lRab[1][1];
+          sc[9] = lRab[1][2] + lRab[2][1];
+          sc[10] = lRab[2][2];
+        }
+      }
+      __syncthreads();
+    }
+    if (a.mode == 1 && act) {
+      const double lI = dO * (sc[0] * nbg * nbg + sc[1] + sc[2] * xh + sc[3] * yh + sc[4] * zh + sc[5] * xh * xh +
+                              sc[6] * xh * yh + sc[7] * xh * zh + sc[8] * yh * yh + sc[9] * yh * zh +
+                              sc[10] * zh * zh);
+      mu[e] = mu[e] + (R)lI * inv_f;
+    }
+    __syncthreads();              // sc and buf are reused by the next cell
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_rd_sub(int mode, const StageArgs &s, bool f32, const void *Istar, const double *Tm,
+                          double *usub, const double *lam_u, void *mu, double *g_aa, double *g_as, double *outTa,
+                          double wTa, double *outTb, double wTb, cudaStream_t st) {
+  RdAdjArgs a;
+  a.mode = mode;
+  a.Istar = Istar;
+  a.mu = mu;
+  a.Tm = Tm;
+  a.rho = s.rho;
+  a.u = s.u;
+  a.aa = s.aa;
+  a.as = s.as;
+  a.usub = usub;
+  a.lam_u = lam_u;
+  a.g_aa = g_aa;
+  a.g_as = g_as;
+  a.outTa = outTa;
+  a.outTb = outTb;
+  a.wTa = wTa;
+  a.wTb = wTb;
+  a.dts = s.dts;
+  a.n1 = s.n1;
+  a.n2 = s.n2;
+  a.n3 = s.n3;
+  a.nap = s.nap;
+  a.nang = s.nang;
+  a.kc = 4;
+  a.cols64 = s.cols64;
+  a.colsR = s.cols;
+  a.dir = s.dir;
+  a.dOmega = s.dOmega;
+  a.zero_guard = s.zero_guard;
+  a.n0crit = s.n0crit;
+  a.a_rad = s.a_rad;
+  a.gamma = s.gamma;
+  a.inv_gm1 = s.inv_gm1;
+  const int threads = (s.nang + 31) / 32 * 32;
+  const unsigned grid = (unsigned)((size_t)s.n1 * s.n2 * ((s.n3 + a.kc - 1) / a.kc));
+  if (f32) k_rd_sub<float><<<grid, threads, 0, st>>>(a);
+  else k_rd_sub<double><<<grid, threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_couple_rd(const StageArgs &s, bool f32, const double *Tm, double *Tout, cudaStream_t st) {
   RdArgs a;

@@ -108,6 +108,13 @@ int check_stage(const StageArgs &a, bool f32, std::string &err);
 // Coupling with the radiation-dominated velocity substitution (raddom.cu):
 // I* in s.Iout -> I+, T- (Tm) -> T+ (Tout), the gas source of stage s.stage2.
 cudaError_t launch_couple_rd(const StageArgs &s, bool f32, const double *Tm, double *Tout, cudaStream_t st);
+// The substitution of the rad_dom option for the adjoint (raddom.cu): mode 0
+// writes the substituted velocity of every cell from the saved I* and T-,
+// mode 1 takes dL/du_sub back to mu, T- (outTa / outTb, weighted) and the
+// opacity gradients.
+cudaError_t launch_rd_sub(int mode, const StageArgs &s, bool f32, const void *Istar, const double *Tm,
+                          double *usub, const double *lam_u, void *mu, double *g_aa, double *g_as, double *outTa,
+                          double wTa, double *outTb, double wTb, cudaStream_t st);
 
 template <typename R> struct GeoTypes;
 template <> struct GeoTypes<double> { using Col = ColGeo; using Face = FaceGeo; };

@@ -20,7 +20,8 @@ whole).  dt = 0.3 x the oracle's time-step bound.
 Samples (numpy PCG64, seed 30): 4096 cells, for torus3d including every
 cell within four of the radial and polar boundaries in a few columns, with
 T, the gas source of the last step and the tetrad-frame moments R there;
-8192 (cell, bin) intensities (oracle bin order).
+8192 (cell, bin) intensities (oracle bin order) and the oracle grid's bin
+directions (to pair its bins with another grid's).
 
     python tests/golden/make_config_samples.py turb3d|torus3d
 
@@ -73,14 +74,17 @@ def step_slabs_x1(w, ang, I, T, gas, dt, slab, setups):
     I2, T2, src = torch.empty_like(I), torch.empty_like(T), torch.empty(T.shape + (4,), dtype=T.dtype)
     for i0 in range(0, n1, slab):
         lo, hi = max(0, i0 - M), min(n1, i0 + slab + M)
-        if i0 not in setups:
+        st = setups.get(i0) if setups is not None else None
+        if st is None:
             bc = ("outflow", "outflow")     # the true boundary where the window reaches it, a cut elsewhere
             xf = [w["xf"][0][lo:hi + 1], w["xf"][1], w["xf"][2]]
-            setups[i0] = Setup(Grid(w["kind"], w["spin"], xf, (bc, w["bc"][1], w["bc"][2]), 3), ang)
+            st = Setup(Grid(w["kind"], w["spin"], xf, (bc, w["bc"][1], w["bc"][2]), 3), ang)
+            if setups is not None:
+                setups[i0] = st
         g = {k: v[:, :, lo:hi].contiguous() for k, v in gas.items() if v is not None}
         g["eta"] = None
-        a, b, c, ok = OS.rk2_step(I[:, :, lo:hi].contiguous(), T[:, :, lo:hi].contiguous(), g, dt, setups[i0],
-                                  OS.Opts())
+        a, b, c, ok = OS.rk2_step(I[:, :, lo:hi].contiguous(), T[:, :, lo:hi].contiguous(), g, dt, st, OS.Opts())
+        del st
         assert bool(ok.all())
         s = slice(i0 - lo, i0 - lo + min(slab, n1 - i0))
         I2[:, :, i0:i0 + slab], T2[:, :, i0:i0 + slab], src[:, :, i0:i0 + slab] = a[:, :, s], b[:, :, s], c[:, :, s]
@@ -107,8 +111,12 @@ def sample_cells(w, rng):
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("name", choices=["turb3d", "torus3d"])
+    p.add_argument("--add-dirs", action="store_true", help="only add the bin directions to an existing file")
     a = p.parse_args()
     w = W.make(a.name, with_intensity=False)
+    if a.add_dirs:
+        add_dirs(os.path.join(HERE, f"{a.name}_samples.npz"), w["level"])
+        return
     ang = GeodesicGrid(w["level"])
     n1, n2, n3 = w["n"]
     if a.name == "turb3d":
@@ -123,13 +131,12 @@ def main():
     T = torch.tensor(w["T"])
     gas = {k: torch.tensor(w[k]) for k in ("rho", "u", "alpha_a", "alpha_s")}
     gas["eta"] = None
-    setups = {}
     for s in range(w["nsteps"]):
         t0 = time.time()
         if a.name == "turb3d":
             I, T, src = step_slabs_x3(w, ang, I, T, gas, dt, 16)
         else:
-            I, T, src = step_slabs_x1(w, ang, I, T, gas, dt, 32, setups)
+            I, T, src = step_slabs_x1(w, ang, I, T, gas, dt, 32, None)   # geometry rebuilt per slab (memory)
         print(f"step {s + 1}/{w['nsteps']} {time.time() - t0:.0f} s", flush=True)
     rng = np.random.default_rng(30)
     cells = sample_cells(w, rng)
@@ -140,8 +147,16 @@ def main():
     vals = I[bcells[:, 0], bcells[:, 1], bcells[:, 2], bins].numpy()
     out = os.path.join(HERE, f"{a.name}_samples.npz")
     np.savez_compressed(out, cells=cells, T=T[kc, jc, ic].numpy(), src=src[kc, jc, ic].numpy(), R=R,
-                        bin_cells=bcells, bins=bins, I=vals, dt=dt, steps=w["nsteps"])
+                        bin_cells=bcells, bins=bins, I=vals, dt=dt, steps=w["nsteps"], dirs=ang.dir.numpy())
     print("wrote", out)
+
+
+def add_dirs(path, level):
+    """Store the oracle grid's bin directions beside values written before
+    they were stored (they pair the oracle's bins with another grid's)."""
+    d = dict(np.load(path))
+    d["dirs"] = GeodesicGrid(level).dir.numpy()
+    np.savez_compressed(path, **d)
 
 
 if __name__ == "__main__":

@@ -23,7 +23,8 @@ metric does not depend on phi, so one phi slab gives the full grid's bound).
 writes tests/golden/torus3d_big_subvolume.npz: R (tetrad-frame moments
 [24, 24, 24, 10]), T [24, 24, 24], src (gas source of the last step
 [24, 24, 24, 4]), I at 8192 seeded (cell, bin) samples (oracle bin order),
-the window, dt, steps and the margin difference.
+the window, dt, steps, the margin difference and the oracle grid's bin
+directions.
 """
 import argparse
 import math
@@ -116,7 +117,7 @@ def main():
     vals = I2.numpy()[cells[:, 0], cells[:, 1], cells[:, 2], bins]
     np.savez_compressed(a.out, R=R.numpy(), T=T2.numpy(), src=src2.numpy(), sample_cells=cells,
                         sample_bins=bins, sample_I=vals, origin=np.array(origin), sub=SUB, steps=STEPS,
-                        dt=dt, margins=np.array(a.margins), margin_diff=diff)
+                        dt=dt, margins=np.array(a.margins), margin_diff=diff, dirs=ang.dir.numpy())
     print("wrote", a.out)
 
 

@@ -484,3 +484,58 @@ def test_ppm_step_vjp_matches_oracle(name, n, level, recon, coupling, C, prec):
     finally:
         gc.close()
 
+
+
+@pytest.mark.parametrize("name,n,level,prec,recon", [
+    ("turb3d", (7, 5, 6), 2, "f64", "plm"),          # flat, moving gas, rho spread over 1e-3 .. 10
+    ("turb3d", (4, 3, 9), 2, "f64", "dc"),
+    ("torus3d", (8, 6, 4), 2, "f64", "plm"),         # Kerr-Schild, gas at rest, torus density x 10
+    ("torus3d_big", (6, 6, 4), 2, "f64", "plm"),     # moving gas and scattering in Kerr-Schild
+    ("turb3d", (7, 5, 6), 2, "f32", "plm"),
+])
+def test_radiation_dominated_step_vjp_matches_oracle(name, n, level, prec, recon):
+    """rad_dom = 1: the adjoint through the substituted velocity against the
+    oracle's reverse mode (FP64 1e-11, dL/dalpha_s 2e-10 as for the thermal
+    adjoint; FP32 2e-4).  The density is spread so that the substitution is
+    active in some cells and not in others."""
+    from oracle import coupling as OC
+    w = _thermal_workload(name, n, level)
+    if name == "turb3d":
+        w["rho"] = 10.0 ** np.random.default_rng(4).uniform(-3, 1, w["T"].shape)
+    else:
+        w["rho"] = 10.0 * w["rho"]
+    st = oracle_setup(w)
+    gc = GpuCase(w)
+    try:
+        gmap = match_bins(gc.dir, st.ang.dir.numpy())
+        dt = OCFL.cfl_dt(st, w["cfl"])
+        act = OC.substituted_velocity(torch.tensor(w["I0"]), torch.tensor(w["T"]), oracle_gas(w), dt, st)[2]
+        assert 0 < int(act.sum()) < act.numel()
+        rng = np.random.default_rng(13)
+        lam, lamT = rng.normal(size=w["I0"].shape), rng.normal(size=w["T"].shape)
+        I0, T0 = torch.tensor(w["I0"]), torch.tensor(w["T"])
+        lam_o, lamT_o, ga_o, gs_o, _ = OA.step_vjp(I0, T0, oracle_gas(w), dt, st,
+                                                   OS.Opts(recon=recon, rad_dom=True),
+                                                   torch.tensor(lam), torch.tensor(lamT))
+        f32 = prec == "f32"
+        tdt = torch.float32 if f32 else torch.float64
+        o = rad.rad_opts_default(precision=rad.RAD_F32 if f32 else rad.RAD_F64, coupling=rad.RAD_COUPLE_THERMAL,
+                                 recon=rad.RAD_RECON_PLM if recon == "plm" else rad.RAD_RECON_DC, rad_dom=1)
+        Ig = gc.to_gpu_I(w["I0"], gmap, tdt)
+        lg = gc.to_gpu_I(lam, gmap, tdt)
+        ln = torch.zeros_like(Ig)
+        gas = gc.gas(w)
+        lTg = torch.tensor(lamT, device="cuda")
+        lTn = torch.zeros_like(lTg)
+        ga = torch.zeros_like(gas["rho"])
+        gs = torch.zeros_like(ga)
+        rad.rad_step_adjoint(gc.ctx, Ig, gas, dt, o, lg, ln, lTg, lTn, ga, gs, None)
+        torch.cuda.synchronize()
+        rad.rad_check(gc.ctx)
+        tol = 2e-4 if f32 else 1e-11
+        assert rel_err(gc.from_gpu_I(ln, gmap), lam_o.numpy()) < tol
+        assert rel_err(lTn.cpu().numpy(), lamT_o.numpy()) < tol
+        assert rel_err(ga.cpu().numpy(), ga_o.numpy()) < tol
+        assert rel_err(gs.cpu().numpy(), gs_o.numpy()) < (2e-4 if f32 else 2e-10)
+    finally:
+        gc.close()

@@ -184,3 +184,61 @@ def test_radiation_dominated_moving_equilibration_converges_to_the_ode():
         assert err < 0.85 * run(nsteps, False)[0]
     assert errs[2] < 0.08
     assert 1.6 < errs[0] / errs[1] < 2.6 and 1.6 < errs[1] / errs[2] < 2.6
+
+
+def test_substituted_coupling_gradient_matches_finite_differences():
+    """The oracle's reverse-mode gradient of one step with the substitution
+    (the reference the GPU adjoint is compared with) against central
+    differences in alpha_a, alpha_s, T^0 and intensities, at cells where the
+    substitution is active with momentum fractions strictly inside (0, 1)
+    (so the velocity depends smoothly on the inputs), on a flat moving-gas
+    block with the density spread over 1e-3 .. 10.  Steps of 1e-4 relative
+    (at 1e-5 roundoff dominates the small opacities' differences)."""
+    import workloads as W
+    from oracle import adjoint as A
+    from oracle.angles import GeodesicGrid
+    from oracle.transport import Grid, Setup
+    w = W.make("turb3d", n=(5, 4, 3), level=1)
+    w["rho"] = 10.0 ** np.random.default_rng(4).uniform(-3, 1, w["T"].shape)
+    st = Setup(Grid(w["kind"], w["spin"], w["xf"], w["bc"], w["ndim"]), GeodesicGrid(1))
+    gas = {k: torch.tensor(w[k]) for k in ("rho", "u", "alpha_a", "alpha_s")}
+    gas["eta"] = None
+    I0, T0 = torch.tensor(w["I0"]), torch.tensor(w["T"])
+    dt = 0.004
+    o = S.Opts(recon="plm", rad_dom=True)
+    u_sub, f, act = C.substituted_velocity(I0, T0, gas, dt, st)
+    interior = act & ((f > 1e-6) & (f < 1 - 1e-6)).all(-1)
+    assert int(interior.sum()) >= 4 and int((~act).sum()) >= 4
+    rng = np.random.default_rng(8)
+    lam, lamT = torch.tensor(rng.normal(size=I0.shape)), torch.tensor(rng.normal(size=T0.shape))
+
+    def obj(I, T, g):
+        I2, T2, _, ok = S.rk2_step(I, T, g, dt, st, o)
+        assert bool(ok.all())
+        return float((I2 * lam).sum() + (T2 * lamT).sum())
+
+    lI, lT, ga, gs, _ = A.step_vjp(I0, T0, gas, dt, st, o, lam, lamT)
+    cells = [tuple(c) for c in interior.nonzero().tolist()[:4]]
+    for c in cells:
+        for key, grad in (("alpha_a", ga), ("alpha_s", gs)):
+            h = 1e-4 * float(gas[key][c])
+            gp, gm = dict(gas), dict(gas)
+            gp[key] = gas[key].clone()
+            gp[key][c] += h
+            gm[key] = gas[key].clone()
+            gm[key][c] -= h
+            fd = (obj(I0, T0, gp) - obj(I0, T0, gm)) / (2 * h)
+            assert abs(fd - float(grad[c])) <= 1e-6 * max(abs(fd), 1e-3 * float(grad.abs().max())), (key, c)
+        h = 1e-4 * float(T0[c])
+        Tp, Tm = T0.clone(), T0.clone()
+        Tp[c] += h
+        Tm[c] -= h
+        fd = (obj(I0, Tp, gas) - obj(I0, Tm, gas)) / (2 * h)
+        assert abs(fd - float(lT[c])) <= 1e-6 * max(abs(fd), 1e-3 * float(lT.abs().max())), ("T", c)
+        for n in (0, 5):
+            h = 1e-4 * float(I0[c + (n,)])
+            Ip, Im = I0.clone(), I0.clone()
+            Ip[c + (n,)] += h
+            Im[c + (n,)] -= h
+            fd = (obj(Ip, T0, gas) - obj(Im, T0, gas)) / (2 * h)
+            assert abs(fd - float(lI[c + (n,)])) <= 1e-6 * max(abs(fd), 1e-3 * float(lI.abs().max())), ("I", c, n)
