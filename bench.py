@@ -352,7 +352,7 @@ def run_ours(args, rank, world):
         else:
             res["e2e"] = run_e2e(args, rad, ctx, dt, opts, prec, mom, sh, na, nap, tdt, dev, world)
     rad.rad_destroy(ctx)
-    if not args.no_extras and rank == 0 and args.precision == "f32":
+    if not args.no_extras and world == 1 and args.precision == "f32":
         res["extras"] = run_extras(args, dev)
     return res
 
@@ -745,7 +745,7 @@ def main():
         torch.distributed.init_process_group("nccl", timeout=datetime.timedelta(seconds=300))
     res = run_ours(args, rank, world)
     if rank == 0:
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:
             res["cpu_baseline"] = oracle_sample()
         print(json.dumps(res), flush=True)
     if world > 1:

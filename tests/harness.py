@@ -120,3 +120,13 @@ def run_both(w, nsteps, precision="f64", recon="plm", coupling=None, dt=None, ta
 def rel_err(a, b):
     """max |a - b| / max |b| (normwise relative error)."""
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def rel_err_elem(a, b):
+    """max |a - b| / |b| over elements with b != 0 (per-element relative
+    error; where b == 0 the two must agree exactly, else inf)."""
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    nz = b != 0
+    if np.any(a[~nz] != 0):
+        return float("inf")
+    return float((np.abs(a[nz] - b[nz]) / np.abs(b[nz])).max()) if nz.any() else 0.0

@@ -131,10 +131,11 @@ def test_argument_errors_are_reported():
         with pytest.raises(rad.RadError) as e:     # rad_dom is a flag
             rad.rad_step(ctx, I, gas, 0.01, rad.rad_opts_default(rad_dom=2))
         assert e.value.status == rad.RAD_EINVAL
-        with pytest.raises(rad.RadError) as e:     # the adjoint does not cover it
-            rad.rad_step_adjoint(ctx, I, gas, 0.01, rad.rad_opts_default(rad_dom=1),
+        with pytest.raises(rad.RadError) as e:     # the adjoint checks the options like the step
+            rad.rad_step_adjoint(ctx, I, gas, 0.01,
+                                 rad.rad_opts_default(rad_dom=1, coupling=rad.RAD_COUPLE_EMISSIVITY),
                                  lam, torch.zeros_like(I), None, None, f(1, 4, 4), f(1, 4, 4))
-        assert e.value.status == rad.RAD_EUNSUPPORTED
+        assert e.value.status == rad.RAD_EINVAL
         rad.rad_step(ctx, I, gas, 0.01, o)         # a valid call on the same context still works
         rad.rad_check(ctx)
     finally:

@@ -2,7 +2,11 @@
 
 Tolerances: FP64 path 1e-12 relative (normwise, max |gpu - oracle| /
 max |oracle| per output array); FP32 path 2e-5 relative for I after the
-listed steps (FP32 transport and coupling sums, FP64 quartic)."""
+listed steps (FP32 transport and coupling sums, FP64 quartic).  Per element
+(max |gpu - oracle| / |oracle|, guarded zeros equal exactly) the intensity
+also holds to 1e-10 (FP64) and 2e-3 (FP32): a dim cell's flux difference
+carries the rounding of its bright neighbours, so the per-element bound is
+the normwise one times the dynamic range of the inputs (256 in turb3d)."""
 import math
 
 import numpy as np
@@ -11,7 +15,7 @@ import torch
 
 import paper_2302_04283_gb300 as rad
 import workloads as W
-from tests.harness import GpuCase, match_bins, rel_err, run_both
+from tests.harness import GpuCase, match_bins, rel_err, rel_err_elem, run_both
 
 pytestmark = pytest.mark.gpu
 
@@ -39,7 +43,9 @@ def test_step_f64_matches_oracle(name, n, level, steps):
     r = run_both(w, steps, "f64")
     try:
         assert rel_err(r["I_g"], r["I_o"]) < TOL64
+        assert rel_err_elem(r["I_g"], r["I_o"]) < 1e-10
         assert rel_err(r["T_g"], r["T_o"]) < TOL64
+        assert rel_err_elem(r["T_g"], r["T_o"]) < 1e-11
         if w["mode"] == "thermal":
             assert rel_err(r["src_g"], r["src_o"]) < 1e-11
         # padding bins are never written
@@ -55,7 +61,9 @@ def test_step_f32_matches_oracle(name, n, level, steps):
     r = run_both(w, steps, "f32")
     try:
         assert rel_err(r["I_g"], r["I_o"]) < TOL32
+        assert rel_err_elem(r["I_g"], r["I_o"]) < 2e-3
         assert rel_err(r["T_g"], r["T_o"]) < TOL32
+        assert rel_err_elem(r["T_g"], r["T_o"]) < 2e-4
     finally:
         r["gc"].close()
 
