@@ -699,15 +699,21 @@ class OracleSample:
 
 
 def oracle_sample(steps=30):
-    o = OracleSample()
-    o.step()
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        o.step()
-    return o.describe(steps, time.perf_counter() - t0)
+    """The oracle's rate in a fresh process (the same code path as the
+    reference arm, so the two numbers differ only by their samples' noise)."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", str(steps),
+           "--warmup", "3"]
+    env = dict(os.environ)
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        env.pop(k, None)
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
+    line = [x for x in r.stdout.splitlines() if x.startswith("{")][-1]
+    return json.loads(line)["cpu_baseline"]
 
 
 def run_reference(args):
+    import torch
+    torch.set_num_threads(os.cpu_count() or 1)
     o = OracleSample()
     for _ in range(args.warmup):
         o.step()
