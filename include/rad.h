@@ -231,7 +231,8 @@ int rad_step(rad_ctx *ctx, void *I, const rad_gas *gas, double dt,
  * calls that overlap on the GPU (other streams or contexts on the same
  * device) race.  The first call on a device, with that device current, looks
  * up the array's device address; make that first call before any stream
- * capture.  Calls no cudaMalloc or cudaFree.
+ * capture.  Calls no cudaMalloc or cudaFree.  Gray transport only: a
+ * context with groups set (rad_set_groups) gives RAD_EUNSUPPORTED.
  */
 int rad_step_noalloc(rad_ctx *ctx, void *I, const rad_gas *gas, double dt,
                      const rad_opts *opts, double *gas_src);
