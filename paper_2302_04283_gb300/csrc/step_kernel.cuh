@@ -170,7 +170,13 @@ __device__ __forceinline__ R face_val(bool upR, bool plm, R a, R b, R c, R d) {
 // and finishes with FP64 steps (Newton with a slope accurate to 1e-7 still
 // gains seven digits per step), falling back to the FP64 iteration when the
 // FP64 residual is not small; the FP64 path iterates in FP64 throughout.
-__device__ __forceinline__ double quartic_root(double B4, double B1, double B0, bool full64, bool &ok) {
+// guess > 0 (the temperature before the coupling, usually close to the
+// root): one Newton step from it first.  f is convex, so from either side
+// the step lands at or above the root; inside the bracket it replaces the
+// upper bound as the start of the monotone iteration (a few steps instead
+// of a few tens when the coupling changes T little).
+__device__ __forceinline__ double quartic_root(double B4, double B1, double B0, bool full64, bool &ok,
+                                               double guess = -1.0) {
   if (!(B1 > 0.0) || !(B4 >= 0.0) || !(B0 <= 0.0)) {
     ok = false;
     return 0.0;
@@ -183,6 +189,11 @@ __device__ __forceinline__ double quartic_root(double B4, double B1, double B0, 
     // is still needed (it is not, unless the FP32 range was exceeded)
     const float b4f = (float)B4, b1f = (float)B1, b0f = (float)B0;
     float tf = fminf(-b0f / b1f, sqrtf(sqrtf(-b0f / b4f)));
+    if (guess > 0.0) {
+      const float g = (float)guess, g3 = g * g * g;
+      const float tg = g - __fdividef(fmaf(fmaf(b4f, g3, b1f), g, b0f), fmaf(4.0f * b4f, g3, b1f));
+      if (tg > 0.0f && tg < tf) tf = tg;
+    }
     for (int it = 0; it < 40; ++it) {
       const float t2 = tf * tf;
       const float f = fmaf(fmaf(b4f, t2 * tf, b1f), tf, b0f);
@@ -204,6 +215,11 @@ __device__ __forceinline__ double quartic_root(double B4, double B1, double B0, 
   }
   // FP64: Newton from the upper bound decreases monotonically onto the root
   double T = fmin(-B0 / B1, sqrt(sqrt(-B0 / B4)));
+  if (guess > 0.0) {
+    const double g3 = guess * guess * guess;
+    const double tg = guess - fma(fma(B4, g3, B1), guess, B0) / fma(4.0 * B4, g3, B1);
+    if (tg > 0.0 && tg < T) T = tg;
+  }
   for (int it = 0; it < 80; ++it) {
     const double t2 = T * T;
     const double f = fma(fma(B4, t2 * T, B1), T, B0);
@@ -234,6 +250,94 @@ __device__ __forceinline__ R warp_reduce4(R v0, R v1, R v2, R v3, int lane) {
   b += __shfl_xor_sync(0xffffffffu, b, 2);
   b += __shfl_xor_sync(0xffffffffu, b, 1);
   return b;
+}
+
+// Warp reduce-scatter of eight values: on return lane l holds the warp sum
+// of value (l >> 2) & 7, so lanes 0, 4, ..., 28 hold values 0 .. 7.  Nine
+// shuffles (two warp_reduce4 calls take twelve) in one five-deep chain.
+template <typename R>
+__device__ __forceinline__ R warp_reduce8(const R (&v)[8], int lane) {
+  const bool hi16 = lane & 16, hi8 = lane & 8, hi4 = lane & 4;
+  R a[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    a[k] = hi16 ? v[4 + k] : v[k];
+    a[k] += __shfl_xor_sync(0xffffffffu, hi16 ? v[k] : v[4 + k], 16);
+  }
+  R b[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    b[k] = hi8 ? a[2 + k] : a[k];
+    b[k] += __shfl_xor_sync(0xffffffffu, hi8 ? a[k] : a[2 + k], 8);
+  }
+  R c = hi4 ? b[1] : b[0];
+  c += __shfl_xor_sync(0xffffffffu, hi4 ? b[0] : b[1], 4);
+  c += __shfl_xor_sync(0xffffffffu, c, 2);
+  c += __shfl_xor_sync(0xffffffffu, c, 1);
+  return c;
+}
+
+// The same for sixteen values: lane l ends with the sum of value (l >> 1)
+// & 15, so lanes 0, 2, ..., 30 hold values 0 .. 15 (sixteen shuffles).
+template <typename R>
+__device__ __forceinline__ R warp_reduce16(const R (&v)[16], int lane) {
+  const bool hi16 = lane & 16, hi8 = lane & 8, hi4 = lane & 4, hi2 = lane & 2;
+  R a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    a[k] = hi16 ? v[8 + k] : v[k];
+    a[k] += __shfl_xor_sync(0xffffffffu, hi16 ? v[k] : v[8 + k], 16);
+  }
+  R b[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    b[k] = hi8 ? a[4 + k] : a[k];
+    b[k] += __shfl_xor_sync(0xffffffffu, hi8 ? a[k] : a[4 + k], 8);
+  }
+  R c[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    c[k] = hi4 ? b[2 + k] : b[k];
+    c[k] += __shfl_xor_sync(0xffffffffu, hi4 ? b[k] : b[2 + k], 4);
+  }
+  R d = hi2 ? c[1] : c[0];
+  d += __shfl_xor_sync(0xffffffffu, hi2 ? c[0] : c[1], 2);
+  d += __shfl_xor_sync(0xffffffffu, d, 1);
+  return d;
+}
+
+// The same for thirty-two values: lane l ends with the sum of value l
+// (thirty-one shuffles).
+template <typename R>
+__device__ __forceinline__ R warp_reduce32(const R (&v)[32], int lane) {
+  const bool hi16 = lane & 16, hi8 = lane & 8, hi4 = lane & 4, hi2 = lane & 2, hi1 = lane & 1;
+  R a[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    a[k] = hi16 ? v[16 + k] : v[k];
+    a[k] += __shfl_xor_sync(0xffffffffu, hi16 ? v[k] : v[16 + k], 16);
+  }
+  R b[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    b[k] = hi8 ? a[8 + k] : a[k];
+    b[k] += __shfl_xor_sync(0xffffffffu, hi8 ? a[k] : a[8 + k], 8);
+  }
+  R c[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    c[k] = hi4 ? b[4 + k] : b[k];
+    c[k] += __shfl_xor_sync(0xffffffffu, hi4 ? b[k] : b[4 + k], 4);
+  }
+  R d[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    d[k] = hi2 ? c[2 + k] : c[k];
+    d[k] += __shfl_xor_sync(0xffffffffu, hi2 ? c[k] : c[2 + k], 2);
+  }
+  R e = hi1 ? d[1] : d[0];
+  e += __shfl_xor_sync(0xffffffffu, hi1 ? d[0] : d[1], 1);
+  return e;
 }
 
 struct Nbr {
@@ -497,7 +601,6 @@ __host__ __device__ constexpr size_t stage_smem(int threads, int nap, int kc, in
          + (size_t)kc * nap * sizeof(R)                         // I* of the chunk
          + (size_t)kc * 5 * sizeof(R)                           // gas ux uy uz alphaE u0
          + (size_t)kc * (threads / 32) * kNRedC * sizeof(R)     // per-warp partial sums
-         + (size_t)kc * kNRedC * sizeof(R)                      // cell sums
          + (size_t)kc * sizeof(R)                               // S per cell
          + (tau ? (size_t)kc * 6 * 5 * sizeof(R) : 0)           // optical-depth data of the six faces
          + (size_t)2 * kMaxStages * 8 + 16;                     // full and empty mbarriers
@@ -557,8 +660,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   R *sI = stg + a.depth * ROWS * nap;                    // [kc][nap]
   R *sgas = sI + a.kc * nap;                             // [kc][5]
   R *red = sgas + a.kc * 5;                                // [kc][nwarp][kNRedC]
-  R *sums = red + a.kc * nwarp * kNRedC;                   // [kc][kNRedC]
-  R *Sc = sums + a.kc * kNRedC;                            // [kc]
+  R *Sc = red + a.kc * nwarp * kNRedC;                     // [kc]
   constexpr bool tau = TAU;                                // optical-depth flux weighting (Sec. 2.4)
   R *stau = Sc + a.kc;                                     // [kc][6 faces][f, u^1, u^2, u^3, u^0 of the neighbour]
   R *gbuf = stau + (tau ? a.kc * 30 : 0);                 // [2][nap][2] MAPR gradients (two cells in turn)
@@ -1078,6 +1180,14 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       const V U0 = P::mul(fconv, sv(sr + SI0 * nap));
       Us = P::mul(P::mk(R(0.5), R(0.5)), P::add(U0, Us));
     }
+    // every read of this ring stage is done: release it to the producer now,
+    // so that the next copies overlap this cell's coupling sums (the
+    // arrive's release semantics order the warp's reads before it)
+    __syncwarp();
+    if (lane == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&ebars[st])) : "memory");
+    }
     const V Is = P::mul(Us, inv_f);
     if (inpair) *(V *)(sI + c * nap + b0) = Is;
     if (a.Istar && inpair) *(V *)((R *)a.Istar + (unsigned)(k0 + c) * strideK + own) = Is;
@@ -1094,12 +1204,6 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       const R s2 = warp_reduce4(v0.x + v0.y, v1.x + v1.y, w.x + w.y, R(0), lane);
       if ((lane & 7) == 0 && lane < 24) red[(c * nwarp + warp) * kNRedC + (lane >> 3)] = s2;
     }
-    // this warp is done with the stage: release it to the producer
-    __syncwarp();
-    if (lane == 0) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&ebars[st])) : "memory");
-    }
     if (++st == a.depth) {
       st = 0;
       ph ^= 1u;
@@ -1109,21 +1213,18 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
 
   if (couple) {
     __syncthreads();
-    // ---- phase B: one thread per cell
-    for (int q = t; q < nc * kNRedA; q += blockDim.x) {
-      const int c = q / kNRedA, r = q % kNRedA;
-      R s = R(0);
-      for (int w = 0; w < nwarp; ++w) s += red[(c * nwarp + w) * kNRedC + r];
-      sums[c * kNRedC + r] = s;
-    }
-    __syncthreads();
+    // ---- phase B: one thread per cell; its gas loads are issued before it
+    // sums the warps' partials, so that their latency overlaps the sums
     if (t < nc) {
       const int c = t, k = k0 + c;
       const unsigned cell = (unsigned)k * ncol + col;
-      const R *rs = sums + c * kNRedC;
-      const double D = (double)rs[0], A2 = a.dts / kFourPi * (double)rs[1], Em = (double)rs[2];
       const double Tst = ST2 ? 0.5 * (a.T0[cell] + a.T1[cell]) : a.T0[cell];
       const double aa = a.aa[cell], as = a.as[cell];
+      R rs[kNRedA] = {R(0), R(0), R(0)};
+      for (int w = 0; w < nwarp; ++w)
+#pragma unroll
+        for (int r = 0; r < kNRedA; ++r) rs[r] += red[(c * nwarp + w) * kNRedC + r];
+      const double D = (double)rs[0], A2 = a.dts / kFourPi * (double)rs[1], Em = (double)rs[2];
       double S, Tp = Tst;
       bool ok = true;
       if (a.mode == RAD_COUPLE_THERMAL) {
@@ -1131,7 +1232,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
         const double B4 = A2 * aa * a.a_rad;
         const double B1 = cv * (1.0 - A2 * as);
         const double B0 = D + A2 * as * Em - B1 * Tst;   // A1 - B1 T- - (1 - A2 alpha_s) Ebar-
-        Tp = quartic_root(B4, B1, B0, sizeof(R) == 8, ok);
+        Tp = quartic_root(B4, B1, B0, sizeof(R) == 8, ok, Tst);
         const double Ep = Em - cv * (Tp - Tst);
         const double T2 = Tp * Tp;
         S = aa * a.a_rad * T2 * T2 + as * Ep;
@@ -1161,10 +1262,10 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   // ---- phase C: implicit update of every bin
   V chk = zero;           // stays 0 unless a written value is not finite (0 * inf, 0 * nan = nan)
   const bool want_src = couple && a.src;
-  for (int c = 0; c < (cons ? nc : 0); ++c) {
-    const unsigned kOff = (unsigned)(k0 + c) * strideK;
-    const V Is = inpair ? *(const V *)(sI + c * nap + b0) : zero;
-    V out = Is;
+  // I+ of one cell before the guard, from I* and the cell's source S
+  auto implicit = [&](int c, V &Is, V &out) {
+    Is = inpair ? *(const V *)(sI + c * nap + b0) : zero;
+    out = Is;
     if (couple) {
       const R *g = sgas + 5 * c;
       const V ux = P::mk(g[0], g[0]), uy = P::mk(g[1], g[1]), uz = P::mk(g[2], g[2]);
@@ -1173,19 +1274,100 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       const V rden = P::rcp(P::fma(nb, P::mk(aEd, aEd), P::mk(n0up, n0up)));
       const V c2n = P::mul(P::mul(P::mk(c2pre, c2pre), rden), P::rcp(P::mul(nb, P::mul(nb, nb))));
       out = P::fma(P::mul(P::mk(n0up, n0up), rden), Is, P::mul(c2n, P::mk(Sc[c], Sc[c])));
-      if (want_src) {
-        // gas source: sums of (I+ - I*) n^A dOmega (taken before the guard)
-        const V d = P::mul(P::sub(out, Is), dOm);
-        const V dx = P::mul(d, nhx), dy = P::mul(d, nhy), dz = P::mul(d, nhz);
-        const R s = warp_reduce4(d.x + d.y, dx.x + dx.y, dy.x + dy.y, dz.x + dz.y, lane);
-        if ((lane & 7) == 0) red[(c * nwarp + warp) * kNRedC + (lane >> 3)] = s;
-      }
     }
+  };
+  // gas source: the pair's share of sum (I+ - I*) n^A dOmega (before the guard)
+  auto src4 = [&](V Is, V out, R (&v)[4]) {
+    const V d = P::mul(P::sub(out, Is), dOm);
+    const V dx = P::mul(d, nhx), dy = P::mul(d, nhy), dz = P::mul(d, nhz);
+    v[0] = d.x + d.y;
+    v[1] = dx.x + dx.y;
+    v[2] = dy.x + dy.y;
+    v[3] = dz.x + dz.y;
+  };
+  auto store = [&](int c, V out) {
     out = P::mul(out, keep);
     if (inpair) {
-      *(V *)(Io + kOff + own) = out;
+      *(V *)(Io + (unsigned)(k0 + c) * strideK + own) = out;
       chk = P::fma(out, zero, chk);
     }
+  };
+  // cells in fours, then pairs: the cells' source sums share one
+  // reduce-scatter and their arithmetic interleaves
+  int c = 0;
+  for (; c + 7 < (cons ? nc : 0); c += 8) {
+    V Is[8], out[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) implicit(c + e, Is[e], out[e]);
+    if (want_src) {
+      R v[32];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        R ve[4];
+        src4(Is[e], out[e], ve);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[4 * e + q] = ve[q];
+      }
+      const R s = warp_reduce32<R>(v, lane);
+      red[((c + (lane >> 2)) * nwarp + warp) * kNRedC + (lane & 3)] = s;
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) store(c + e, out[e]);
+  }
+  for (; c + 3 < (cons ? nc : 0); c += 4) {
+    V Is[4], out[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) implicit(c + e, Is[e], out[e]);
+    if (want_src) {
+      R v[16];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        R ve[4];
+        src4(Is[e], out[e], ve);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[4 * e + q] = ve[q];
+      }
+      const R s = warp_reduce16<R>(v, lane);
+      if ((lane & 1) == 0) {
+        const int q = lane >> 1;
+        red[((c + (q >> 2)) * nwarp + warp) * kNRedC + (q & 3)] = s;
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) store(c + e, out[e]);
+  }
+  for (; c + 1 < (cons ? nc : 0); c += 2) {
+    V Isa, outa, Isb, outb;
+    implicit(c, Isa, outa);
+    implicit(c + 1, Isb, outb);
+    if (want_src) {
+      R v[8], va[4], vb[4];
+      src4(Isa, outa, va);
+      src4(Isb, outb, vb);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        v[q] = va[q];
+        v[4 + q] = vb[q];
+      }
+      const R s = warp_reduce8<R>(v, lane);
+      if ((lane & 3) == 0) {
+        const int q = lane >> 2;
+        red[((c + (q >> 2)) * nwarp + warp) * kNRedC + (q & 3)] = s;
+      }
+    }
+    store(c, outa);
+    store(c + 1, outb);
+  }
+  if (cons && c < nc) {
+    V Is, out;
+    implicit(c, Is, out);
+    if (want_src) {
+      R v[4];
+      src4(Is, out, v);
+      const R s = warp_reduce4(v[0], v[1], v[2], v[3], lane);
+      if ((lane & 7) == 0) red[(c * nwarp + warp) * kNRedC + (lane >> 3)] = s;
+    }
+    store(c, out);
   }
   const bool bad = !isfinite(chk.x) || !isfinite(chk.y);
   if (cons && __any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.err, kErrNonFinite);
