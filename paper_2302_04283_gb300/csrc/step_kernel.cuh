@@ -340,6 +340,27 @@ __device__ __forceinline__ R warp_reduce32(const R (&v)[32], int lane) {
   return e;
 }
 
+// A cell's staged gas values (ux, uy, uz, alpha_E, u0) read with two
+// vector loads from its 8-element row, returned through a small array.
+template <typename R> struct GasRow { R v[8]; };
+__device__ __forceinline__ GasRow<float> gas_load(const float *row) {
+  GasRow<float> g;
+  const float4 a = *(const float4 *)row, b = *(const float4 *)(row + 4);
+  g.v[0] = a.x; g.v[1] = a.y; g.v[2] = a.z; g.v[3] = a.w;
+  g.v[4] = b.x; g.v[5] = b.y; g.v[6] = b.z; g.v[7] = b.w;
+  return g;
+}
+__device__ __forceinline__ GasRow<double> gas_load(const double *row) {
+  GasRow<double> g;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double2 a = *(const double2 *)(row + 2 * q);
+    g.v[2 * q] = a.x;
+    g.v[2 * q + 1] = a.y;
+  }
+  return g;
+}
+
 struct Nbr {
   long long col_off;  // (jj * n1 + ii) * nap
   int kshift;         // 0 or n3 / 2 (polar)
@@ -599,7 +620,7 @@ __host__ __device__ constexpr size_t stage_smem(int threads, int nap, int kc, in
   return (size_t)depth * rows * nap * sizeof(R)                 // staged stencil rows
          + (mapr ? (size_t)4 * nap * sizeof(R) : 0)             // MAPR gradients of two cells
          + (size_t)kc * nap * sizeof(R)                         // I* of the chunk
-         + (size_t)kc * 5 * sizeof(R)                           // gas ux uy uz alphaE u0
+         + (size_t)kc * 8 * sizeof(R)                           // gas ux uy uz alphaE u0 (+3 pad: vector loads)
          + (size_t)kc * (threads / 32) * kNRedC * sizeof(R)     // per-warp partial sums
          + (size_t)kc * sizeof(R)                               // S per cell
          + (tau ? (size_t)kc * 6 * 5 * sizeof(R) : 0)           // optical-depth data of the six faces
@@ -658,8 +679,8 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   // shared memory: staged rows, I* of the chunk, then small per-cell arrays
   R *stg = (R *)smem_raw;                                  // [depth][ROWS][nap]
   R *sI = stg + a.depth * ROWS * nap;                    // [kc][nap]
-  R *sgas = sI + a.kc * nap;                             // [kc][5]
-  R *red = sgas + a.kc * 5;                                // [kc][nwarp][kNRedC]
+  R *sgas = sI + a.kc * nap;                             // [kc][8]
+  R *red = sgas + a.kc * 8;                                // [kc][nwarp][kNRedC]
   R *Sc = red + a.kc * nwarp * kNRedC;                     // [kc]
   constexpr bool tau = TAU;                                // optical-depth flux weighting (Sec. 2.4)
   R *stau = Sc + a.kc;                                     // [kc][6 faces][f, u^1, u^2, u^3, u^0 of the neighbour]
@@ -671,11 +692,11 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
     const unsigned cell = (unsigned)(k0 + c) * ncol + col;
     if (couple || tau) {
       const R ux = (R)a.u[3 * cell], uy = (R)a.u[3 * cell + 1], uz = (R)a.u[3 * cell + 2];
-      sgas[5 * c + 0] = ux;
-      sgas[5 * c + 1] = uy;
-      sgas[5 * c + 2] = uz;
-      sgas[5 * c + 3] = (R)a.aa[cell] + (R)a.as[cell];
-      sgas[5 * c + 4] = sqrt(R(1) + ux * ux + uy * uy + uz * uz);
+      sgas[8 * c + 0] = ux;
+      sgas[8 * c + 1] = uy;
+      sgas[8 * c + 2] = uz;
+      sgas[8 * c + 3] = (R)a.aa[cell] + (R)a.as[cell];
+      sgas[8 * c + 4] = sqrt(R(1) + ux * ux + uy * uy + uz * uz);
     }
   }
   if (tau) {
@@ -1005,7 +1026,8 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
     // optical-depth factors d of the six faces (zero without the weighting)
     V dlo[3] = {zero, zero, zero}, dhi[3] = {zero, zero, zero};
     if (tau) {
-      const R *g = sgas + 5 * c;
+      const GasRow<R> grow = gas_load(sgas + 8 * c);
+      const R *g = grow.v;
       const V io = P::rcp(P::sub(P::mk(g[4], g[4]), P::fma(P::mk(g[2], g[2]), nhz,
                                  P::fma(P::mk(g[1], g[1]), nhy, P::mul(P::mk(g[0], g[0]), nhx)))));
 #pragma unroll
@@ -1192,7 +1214,8 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
     if (inpair) *(V *)(sI + c * nap + b0) = Is;
     if (a.Istar && inpair) *(V *)((R *)a.Istar + (unsigned)(k0 + c) * strideK + own) = Is;
     if (couple) {
-      const R *g = sgas + 5 * c;
+      const GasRow<R> grow = gas_load(sgas + 8 * c);
+      const R *g = grow.v;
       const V ux = P::mk(g[0], g[0]), uy = P::mk(g[1], g[1]), uz = P::mk(g[2], g[2]);
       const R aEd = g[3] * dts;
       const V nb = P::sub(P::mk(g[4], g[4]), P::fma(uz, nhz, P::fma(uy, nhy, P::mul(ux, nhx))));
@@ -1211,6 +1234,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   }
   if (timeout) atomicOr(a.err, 1 << 3);
 
+  double psrc[4] = {0.0, 0.0, 0.0, 0.0};
   if (couple) {
     __syncthreads();
     // ---- phase B: one thread per cell; its gas loads are issued before it
@@ -1218,6 +1242,10 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
     if (t < nc) {
       const int c = t, k = k0 + c;
       const unsigned cell = (unsigned)k * ncol + col;
+      if (ST2 && a.src) {                  // stage 1's share of the source, added to in phase D
+#pragma unroll
+        for (int m = 0; m < 4; ++m) psrc[m] = a.src[4 * cell + m];
+      }
       const double Tst = ST2 ? 0.5 * (a.T0[cell] + a.T1[cell]) : a.T0[cell];
       const double aa = a.aa[cell], as = a.as[cell];
       R rs[kNRedA] = {R(0), R(0), R(0)};
@@ -1267,7 +1295,8 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
     Is = inpair ? *(const V *)(sI + c * nap + b0) : zero;
     out = Is;
     if (couple) {
-      const R *g = sgas + 5 * c;
+      const GasRow<R> grow = gas_load(sgas + 8 * c);
+      const R *g = grow.v;
       const V ux = P::mk(g[0], g[0]), uy = P::mk(g[1], g[1]), uz = P::mk(g[2], g[2]);
       const R aEd = g[3] * dts;
       const V nb = P::sub(P::mk(g[4], g[4]), P::fma(uz, nhz, P::fma(uy, nhy, P::mul(ux, nhx))));
@@ -1388,7 +1417,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         R dR = n0up * (cg.M[m][0] * xs[0] + cg.M[m][1] * xs[1] + cg.M[m][2] * xs[2] + cg.M[m][3] * xs[3]);
-        sp[m] = ST2 ? sp[m] - (double)dR : -0.5 * (double)dR;
+        sp[m] = ST2 ? psrc[m] - (double)dR : -0.5 * (double)dR;
       }
     }
   }
