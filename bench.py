@@ -577,30 +577,36 @@ def run_e2e(args, rad, ctx, dt, opts, prec, mom, sh, na, nap, tdt, dev, world):
         hR = torch.empty(sh + (10,), dtype=tdt, pin_memory=True)
         items.append(dict(hgas, I=hI, eta=None, T=hT, R=hR))
     seq = lambda n: [items[q % len(items)] for q in range(n)]
+    # this machine's pinned host-to-device rate (copies of the intensity
+    # array just before and just after the timed region): the step rate the
+    # uploads alone allow.  The host link may be shared with other work, so
+    # both ends are reported.
+    dI = torch.empty_like(hI, device=dev)
+    s = torch.cuda.current_stream()
+
+    def link_gbs():
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        dI.copy_(hI, non_blocking=True)
+        e0.record(s)
+        dI.copy_(hI, non_blocking=True)
+        e1.record(s)
+        torch.cuda.synchronize()
+        return hI.numel() * hI.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
     rad.rad_step_host(ctx, seq(max(1, args.warmup)), dt, opts, 1, rad.RAD_FRAME_TETRAD, mom)
-    torch.cuda.synchronize()
+    gbs_before = link_gbs()
     t0 = time.perf_counter()
     rad.rad_step_host(ctx, seq(args.steps), dt, opts, 1, rad.RAD_FRAME_TETRAD, mom)
     el = time.perf_counter() - t0
+    h2d_gbs = link_gbs()
+    del dI
     rate = job_rate(sh[0] * sh[1] * sh[2] * na * args.steps, el, dev, world)
     h2d = hI.numel() * hI.element_size() + sum(v.numel() * v.element_size() for v in hgas.values()) + \
         hT.numel() * hT.element_size()
     d2h = hR.numel() * hR.element_size() + hT.numel() * hT.element_size()
-    # this machine's pinned host-to-device rate (one copy of the intensity
-    # array, after the timed region): the step rate the uploads alone allow
-    dI = torch.empty_like(hI, device=dev)
-    s = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    dI.copy_(hI, non_blocking=True)
-    e0.record(s)
-    dI.copy_(hI, non_blocking=True)
-    e1.record(s)
-    torch.cuda.synchronize()
-    h2d_gbs = hI.numel() * hI.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9
-    del dI
     return {"value": rate, "unit": "cell-angle updates/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "h2d_gbs_measured": round(h2d_gbs, 1),
+            "h2d_gbs_measured": round(h2d_gbs, 1), "h2d_gbs_before": round(gbs_before, 1),
             "upload_bound_value": sh[0] * sh[1] * sh[2] * na / (h2d / (h2d_gbs * 1e9)),
             "api": "rad_step_host (host buffers; uploads, read-backs and moments on their own streams, overlapping the steps)",
             "reads_back": "the step's results: moments R^{AB} [cell][10] and gas temperature T [cell]; the evolved "
