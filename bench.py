@@ -671,7 +671,7 @@ class OracleSample:
     """The FP64 oracle on a bounded sample of the workload: the same recipe on
     an n-cell periodic block (setup excluded from timing)."""
 
-    def __init__(self, n=(16, 16, 16)):
+    def __init__(self, n=(24, 24, 24)):
         import torch
         import workloads as W
         from oracle import cfl as OCFL
@@ -704,7 +704,7 @@ class OracleSample:
                           f"recipe, {steps} RK2 steps + moments, FP64 ({el:.1f} s timed)"}
 
 
-def oracle_sample(steps=30):
+def oracle_sample(steps=40):
     """The oracle's rate in a fresh process (the same code path as the
     reference arm, so the two numbers differ only by their samples' noise)."""
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", str(steps),
@@ -734,8 +734,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded turbulent-gas workload; no dataset in the paper)",
             "config": {"workload": WORKLOAD_TEXT, "cells": 128 ** 3, "bins": 162,
-                       "sample": "each step advances a 16^3-cell block of the same recipe (bounded CPU work); "
-                                 "the rate is per cell-angle update, comparable with the GPU arm"},
+                       "sample": f"each step advances a {o.n[0]}^3-cell block of the same recipe (bounded CPU "
+                                 "work); the rate is per cell-angle update, comparable with the GPU arm"},
             "cpu_baseline": info, "e2e": {"value": v, "unit": "cell-angle updates/s",
                                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
