@@ -536,17 +536,20 @@ __device__ __forceinline__ void ppm_states(const typename P2<R>::V (&a)[7], type
 
 // face_div in weighted form (no selects in the cell loop): ncmL / ncmR are
 // -(lower-face coefficient) where the upwind state is the left / right one
-// and 0 otherwise; cpL / cpR likewise for the upper face.
+// and 0 otherwise, cpL / cpR likewise for the upper face, and
+//   div = ncmL (m1 + qm) + ncmR (c - qc) + cpL (c + qc) + cpR (p1 - qp)
+// is evaluated with the own cell's terms gathered: A = ncmR + cpL multiplies
+// c and B = cpL - ncmR the own slope qc (six multiply-adds instead of four
+// sums and four multiply-adds).
 template <typename R>
-__device__ __forceinline__ typename P2<R>::V face_div_w(typename P2<R>::V ncmL, typename P2<R>::V ncmR,
-                                                      typename P2<R>::V cpL, typename P2<R>::V cpR,
+__device__ __forceinline__ typename P2<R>::V face_div_g(typename P2<R>::V ncmL, typename P2<R>::V cpR,
+                                                      typename P2<R>::V A, typename P2<R>::V B,
                                                       typename P2<R>::V m1, typename P2<R>::V c,
                                                       typename P2<R>::V p1, typename P2<R>::V qm,
                                                       typename P2<R>::V qc, typename P2<R>::V qp, bool plm) {
   using P = P2<R>;
-  if (!plm) return P::fma(ncmR, c, P::fma(ncmL, m1, P::fma(cpR, p1, P::mul(cpL, c))));
-  const auto loL = P::add(m1, qm), loR = P::sub(c, qc), hiL = P::add(c, qc), hiR = P::sub(p1, qp);
-  return P::fma(ncmR, loR, P::fma(ncmL, loL, P::fma(cpR, hiR, P::mul(cpL, hiL))));
+  if (!plm) return P::fma(ncmL, m1, P::fma(cpR, p1, P::mul(A, c)));
+  return P::fma(ncmL, qm, P::fma(P::mk(-cpR.x, -cpR.y), qp, P::fma(B, qc, P::fma(ncmL, m1, P::fma(cpR, p1, P::mul(A, c))))));
 }
 
 // face_div with the optical-depth factors of Sec. 2.4: at a face with cells
@@ -799,18 +802,20 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   }
   // weighted coefficients for the flat kernels (the curved ones keep the
   // select form: their registers go to the angular-flux coefficients)
-  V ncmL[3], ncmR[3], cpL[3], cpR[3];
+  V ncmL[3], ncmR[3], cpL[3], cpR[3], gA[3], gB[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     ncmR[d] = P::mk((um[d] & 1) ? -cm[d].x : R(0), (um[d] & 2) ? -cm[d].y : R(0));
     ncmL[d] = P::mk((um[d] & 1) ? R(0) : -cm[d].x, (um[d] & 2) ? R(0) : -cm[d].y);
     cpR[d] = P::mk((up[d] & 1) ? cp[d].x : R(0), (up[d] & 2) ? cp[d].y : R(0));
     cpL[d] = P::mk((up[d] & 1) ? R(0) : cp[d].x, (up[d] & 2) ? R(0) : cp[d].y);
+    gA[d] = P::add(ncmR[d], cpL[d]);
+    gB[d] = P::sub(cpL[d], ncmR[d]);
   }
   auto divd = [&](int d, V m1, V c, V p1, V qm, V qc, V qp, V dl, V dh) -> V {
     if (tau) return face_div_tau<R>(um[d], up[d], cm[d], cp[d], m1, c, p1, qm, qc, qp, dl, dh);
     if (ANG) return face_div<R>(um[d], up[d], cm[d], cp[d], m1, c, p1, qm, qc, qp);
-    return face_div_w<R>(ncmL[d], ncmR[d], cpL[d], cpR[d], m1, c, p1, qm, qc, qp, plm);
+    return face_div_g<R>(ncmL[d], cpR[d], gA[d], gB[d], m1, c, p1, qm, qc, qp, plm);
   };
   // the same from given face states (loL | loR at the lower face, hiL | hiR at the upper)
   auto divs = [&](int d, V loL, V loR, V hiL, V hiR, V dl, V dh) -> V {
@@ -1231,10 +1236,12 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       const R aEd = g[3] * dts;
       const V nb = P::sub(P::mk(g[4], g[4]), P::fma(uz, nhz, P::fma(uy, nhy, P::mul(ux, nhx))));
       const V nbaE = P::mul(nb, P::mk(aEd, aEd));
-      const V rden = P::rcp(P::add(P::mk(n0up, n0up), nbaE));
+      // r2 = 1 / (n^0bar den), den = n^0 + n^0bar alpha_E dt: one reciprocal
+      // gives both 1 / den = n^0bar r2 and dOmega / (n^0bar den)
+      const V r2 = P::rcp(P::mul(nb, P::add(P::mk(n0up, n0up), nbaE)));
       const V w = P::mul(P::mul(Is, P::mul(nb, nb)), dOm);                 // Ibar dOmega_bar
-      const V v0 = P::mul(P::mul(P::mk(-nbaE.x, -nbaE.y), rden), w);     // (c1 - 1) Ibar dOmega_bar
-      const V v1 = P::mul(P::mul(dOm, rden), P::rcp(nb));                 // dOmega / (n^0bar den)
+      const V v0 = P::mul(P::mul(P::mk(-nbaE.x, -nbaE.y), P::mul(nb, r2)), w);   // (c1 - 1) Ibar dOmega_bar
+      const V v1 = P::mul(dOm, r2);                                          // dOmega / (n^0bar den)
       const R s2 = warp_reduce4(v0.x + v0.y, v1.x + v1.y, w.x + w.y, R(0), lane);
       if ((lane & 7) == 0 && lane < 24) red[(c * nwarp + warp) * kNRedC + (lane >> 3)] = s2;
     }
@@ -1311,9 +1318,11 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       const V ux = P::mk(g[0], g[0]), uy = P::mk(g[1], g[1]), uz = P::mk(g[2], g[2]);
       const R aEd = g[3] * dts;
       const V nb = P::sub(P::mk(g[4], g[4]), P::fma(uz, nhz, P::fma(uy, nhy, P::mul(ux, nhx))));
-      const V rden = P::rcp(P::fma(nb, P::mk(aEd, aEd), P::mk(n0up, n0up)));
-      const V c2n = P::mul(P::mul(P::mk(c2pre, c2pre), rden), P::rcp(P::mul(nb, P::mul(nb, nb))));
-      out = P::fma(P::mul(P::mk(n0up, n0up), rden), Is, P::mul(c2n, P::mk(Sc[c], Sc[c])));
+      // q = 1 / (den n^0bar^3): c2 / n^0bar^3 = c2pre q and n^0 / den = n^0 n^0bar^3 q
+      const V nb3 = P::mul(nb, P::mul(nb, nb));
+      const V q = P::rcp(P::mul(P::fma(nb, P::mk(aEd, aEd), P::mk(n0up, n0up)), nb3));
+      const V c2n = P::mul(P::mk(c2pre, c2pre), q);
+      out = P::fma(P::mul(P::mul(P::mk(n0up, n0up), nb3), q), Is, P::mul(c2n, P::mk(Sc[c], Sc[c])));
     }
   };
   // gas source: the pair's share of sum (I+ - I*) n^A dOmega (before the guard)
