@@ -577,21 +577,23 @@ def run_e2e(args, rad, ctx, dt, opts, prec, mom, sh, na, nap, tdt, dev, world):
         hR = torch.empty(sh + (10,), dtype=tdt, pin_memory=True)
         items.append(dict(hgas, I=hI, eta=None, T=hT, R=hR))
     seq = lambda n: [items[q % len(items)] for q in range(n)]
-    # this machine's pinned host-to-device rate (copies of the intensity
-    # array just before and just after the timed region): the step rate the
-    # uploads alone allow.  The host link may be shared with other work, so
-    # both ends are reported.
+    # this machine's sustained pinned host-to-device rate (four back-to-back
+    # copies of the intensity array, just before and just after the timed
+    # region): the step rate the uploads alone allow.  The sustained rate of
+    # the host link varies over time on a shared machine (a single copy does
+    # not show it), so both ends are reported.
     dI = torch.empty_like(hI, device=dev)
     s = torch.cuda.current_stream()
 
-    def link_gbs():
+    def link_gbs(n=4):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         dI.copy_(hI, non_blocking=True)
         e0.record(s)
-        dI.copy_(hI, non_blocking=True)
+        for _ in range(n):
+            dI.copy_(hI, non_blocking=True)
         e1.record(s)
         torch.cuda.synchronize()
-        return hI.numel() * hI.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        return n * hI.numel() * hI.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9
 
     rad.rad_step_host(ctx, seq(max(1, args.warmup)), dt, opts, 1, rad.RAD_FRAME_TETRAD, mom)
     gbs_before = link_gbs()
