@@ -34,6 +34,8 @@ CASES = [
     ("adjoint2d", (10, 8, 1), 2, 2),              # 2D Kerr-Schild, fixed emissivity
     ("turb3d", (4, 3, 37), 2, 1),                 # x3 longer than one 32-cell chunk, ragged tail
     ("torus3d_big", (3, 4, 10), 8, 1),            # 642 bins: FP64 ring two stages deep
+    ("turb3d", (5, 4, 45), 4, 1),                 # the level-4 fixed-row kernel: chunks of 32 + 13 cells
+    ("turb3d", (4, 4, 38), 4, 2),                 # ... and 32 + 6 (phase C in eights, fours, pairs, ones)
 ]
 
 
@@ -55,7 +57,8 @@ def test_step_f64_matches_oracle(name, n, level, steps):
         r["gc"].close()
 
 
-@pytest.mark.parametrize("name,n,level,steps", [CASES[0], CASES[2], CASES[4], CASES[6], CASES[8], CASES[9]])
+@pytest.mark.parametrize("name,n,level,steps", [CASES[0], CASES[2], CASES[4], CASES[6], CASES[8], CASES[9],
+                                                 CASES[10], CASES[11]])
 def test_step_f32_matches_oracle(name, n, level, steps):
     w = W.make(name, n=n, level=level)
     r = run_both(w, steps, "f32")
