@@ -81,6 +81,10 @@ const char *rad_last_error(const rad_ctx *ctx);
  * great-circle arcs through the projected triangle centroids).
  * n_ang = 10 N^2 + 2; n_ang_padded rounds it up to a multiple of 4.
  * Orientation: a pentagon centred on +3hat, the 2hat axis a two-fold axis.
+ * Bin numbering: the library's own (rad_get_angles gives each bin's
+ * direction).  Bins 2t and 2t + 1 have no direction component of opposite
+ * sign wherever the grid allows such a pairing (levels 3, 4, 5, 7, 8, 9,
+ * ...); the flat-space stage kernels use it.
  * level must be in [1, 32].  Synchronous; replaces any previous grid (and
  * invalidates the metric, which must be set again).
  */

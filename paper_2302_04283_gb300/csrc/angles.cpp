@@ -11,10 +11,13 @@
 // point is bounded by great-circle arcs through the projected centroids of
 // the lattice triangles around it.  Solid angles are sums of
 // Van Oosterom-Strackee triangle areas over the fan from the cell centre.
+// The cells are numbered so that cells 2t and 2t + 1 have no direction
+// component of opposite sign wherever the grid allows it (pair_by_sign).
 #include <algorithm>
 #include <array>
 #include <cmath>
 #include <map>
+#include <numeric>
 
 #include "rad_internal.h"
 
@@ -51,6 +54,70 @@ uint64_t lattice_key(std::array<std::pair<int, int>, 3> w) {
     key = key * 1024u + (uint64_t)(p.first * 64 + p.second);
   }
   return key;
+}
+
+// Renumber the lattice points so that points 2t and 2t + 1 have no
+// coordinate of opposite sign (a zero coordinate agrees with either sign).
+// A thread of the stage kernel owns such a pair of bins, so in flat
+// Cartesian space both of its bins take their upwind states from the same
+// side of the cell in every dimension.  Greedy matching: the points with
+// the most nonzero coordinates first, in order of sign pattern, each taking
+// the next unmatched compatible point (one of its own pattern when any is
+// left, since those follow it in this order).  Points left without a partner
+// are paired in order at the end; returns whether there were none.
+bool pair_by_sign(std::vector<V3> &flat, std::vector<std::array<int, 3>> &tris) {
+  const int n = (int)flat.size();
+  std::vector<std::array<int, 3>> sg(n);
+  std::vector<int> nnz(n, 0);
+  for (int a = 0; a < n; ++a) {
+    const double c[3] = {flat[a].x, flat[a].y, flat[a].z};
+    const double tol = 1e-12 * norm(flat[a]);
+    for (int k = 0; k < 3; ++k) {
+      sg[a][k] = c[k] > tol ? 1 : (c[k] < -tol ? -1 : 0);
+      nnz[a] += sg[a][k] != 0;
+    }
+  }
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (nnz[a] != nnz[b]) return nnz[a] > nnz[b];
+    return sg[a] < sg[b];
+  });
+  auto compatible = [&](int a, int b) {
+    for (int k = 0; k < 3; ++k)
+      if (sg[a][k] * sg[b][k] < 0) return false;
+    return true;
+  };
+  std::vector<char> used(n, 0);
+  std::vector<int> seq, rest;
+  seq.reserve(n);
+  for (int ia = 0; ia < n; ++ia) {
+    const int a = order[ia];
+    if (used[a]) continue;
+    used[a] = 1;
+    int pick = -1;
+    for (int ib = ia + 1; ib < n && pick < 0; ++ib)
+      if (!used[order[ib]] && compatible(a, order[ib])) pick = order[ib];
+    if (pick < 0) {
+      rest.push_back(a);
+      continue;
+    }
+    used[pick] = 1;
+    seq.push_back(a);
+    seq.push_back(pick);
+  }
+  const bool all = rest.empty();
+  seq.insert(seq.end(), rest.begin(), rest.end());
+  std::vector<int> newid(n);
+  std::vector<V3> f2(n);
+  for (int i = 0; i < n; ++i) {
+    newid[seq[i]] = i;
+    f2[i] = flat[seq[i]];
+  }
+  flat.swap(f2);
+  for (auto &t : tris)
+    for (int k = 0; k < 3; ++k) t[k] = newid[t[k]];
+  return all;
 }
 
 // Bin of the direction rotated by pi about 2hat, (x, y, z) -> (-x, y, -z),
@@ -213,6 +280,7 @@ bool build_geodesic(int N, AngleGrid &g, std::string &err) {
     err = "geodesic grid has the wrong cell count";
     return false;
   }
+  const bool paired = pair_by_sign(flat, tris);
   std::vector<V3> dir(n_ang);
   for (int n = 0; n < n_ang; ++n) dir[n] = unit(flat[n]);
 
@@ -234,6 +302,7 @@ bool build_geodesic(int N, AngleGrid &g, std::string &err) {
   g = AngleGrid();
   g.level = N;
   g.n_ang = n_ang;
+  g.sign_pairs = paired;
   g.n_ap = (n_ang + 3) / 4 * 4;
   g.dir.resize(3 * n_ang);
   g.dOmega.resize(n_ang);

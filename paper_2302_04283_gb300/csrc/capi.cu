@@ -542,6 +542,8 @@ int rad_check(rad_ctx *ctx) {
   if (h & (1 << 3)) return fail(ctx, RAD_ECUDA, "a device wait timed out (stage pipeline or tensor-core moments)");
   if (h & rad::kErrNoConv) return fail(ctx, RAD_ENOCONV, "a cell's quartic had no bracketed root or did not converge");
   if (h & rad::kErrNonFinite) return fail(ctx, RAD_ENONFINITE, "a non-finite intensity was produced");
+  if (h & rad::kErrState)
+    return fail(ctx, RAD_ESTATE, "the stage kernel met a bin pair with opposite upwind sides (angle numbering)");
   return RAD_OK;
 }
 

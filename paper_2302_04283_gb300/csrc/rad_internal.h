@@ -21,10 +21,12 @@ constexpr int kMaxBehind = 4;            // sides whose line reconstruction read
 // error bits of the sticky device word (bit k <-> status -k)
 constexpr int kErrNoConv = 1 << 4;       // RAD_ENOCONV = -4
 constexpr int kErrNonFinite = 1 << 5;    // RAD_ENONFINITE = -5
+constexpr int kErrState = 1 << 6;        // RAD_ESTATE = -6: tables inconsistent with the kernel's assumptions
 
 // Host description of the geodesic grid (Sec. 2.6); built by angles.cpp.
 struct AngleGrid {
   int level = 0, n_ang = 0, n_ap = 0, n_edge = 0;
+  bool sign_pairs = false;        // bins 2t, 2t + 1 have no direction component of opposite sign
   std::vector<double> dir;        // [n_ang][3]
   std::vector<double> dOmega;     // [n_ang]
   std::vector<int> nbr;           // [n_ang][6], -1 padded

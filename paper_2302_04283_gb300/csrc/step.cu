@@ -87,7 +87,7 @@ cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st
   bool ext = a.divF != nullptr;             // halo rows or a frequency divergence: the run-time-row kernels
   for (int f = 0; f < 6; ++f) ext |= a.halo[f] != nullptr;
   if (ext && !(ang && a.recon_ang != RAD_RECON_DC)) {
-    if (f32 && !ang && a.nap == kNapGeo4) return launch_stage_rp<float, false, 0, -kNapGeo4>(a, st);
+    if (f32 && !ang && a.nap == kNapGeo4 && a.sign_pairs) return launch_stage_rp<float, false, 0, -kNapGeo4>(a, st);
     if (f32) return ang ? launch_stage_rp<float, true>(a, st) : launch_stage_rp<float, false>(a, st);
     return ang ? launch_stage_rp<double, true>(a, st) : launch_stage_rp<double, false>(a, st);
   }
@@ -95,7 +95,7 @@ cudaError_t launch_stage(const StageArgs &a, bool f32, bool ang, cudaStream_t st
     return f32 ? launch_stage_rp<float, true, 1>(a, st) : launch_stage_rp<double, true, 1>(a, st);
   if (ang && a.recon_ang == RAD_RECON_MAPR)
     return f32 ? launch_stage_rp<float, true, 2>(a, st) : launch_stage_rp<double, true, 2>(a, st);
-  if (f32 && !ang && a.nap == kNapGeo4) return launch_stage_rp<float, false, 0, kNapGeo4>(a, st);
+  if (f32 && !ang && a.nap == kNapGeo4 && a.sign_pairs) return launch_stage_rp<float, false, 0, kNapGeo4>(a, st);
   if (f32 && ang) {
     if (a.nap == kNapGeo4) return launch_stage_rp<float, true, 0, kNapGeo4>(a, st);
     if (a.nap == kNapGeo6) return launch_stage_rp<float, true, 0, kNapGeo6>(a, st);
@@ -123,6 +123,7 @@ StageArgs make_stage_args(rad_ctx *ctx, const rad_gas *gas, double dt, const rad
   a.n3 = G.n[2];
   a.nap = ctx->ang.n_ap;
   a.nang = ctx->ang.n_ang;
+  a.sign_pairs = ctx->ang.sign_pairs ? 1 : 0;
   a.ndim = G.ndim;
   // ring depth and cells per CTA along x3: a 3-stage ring (2 when the bins
   // are too many for a chunk of min(n3, 8) cells within the shared-memory

@@ -64,6 +64,7 @@ struct StageArgs {
   int stage2;             // 0: U* = U^0 + dt L;  1: U* = U^0/2 + (U^1 + dt L)/2
   double dt, dts;         // full step and coupling step (dt, then dt/2)
   int n1, n2, n3, nap, nang, ndim, kc;
+  int sign_pairs;         // bins 2t, 2t + 1 have no direction component of opposite sign
   int depth;                       // stages of the shared-memory ring (2..kMaxStages)
   int bc_lo[3], bc_hi[3];
   const void *cols;       // ColGeo or ColGeoF
@@ -812,6 +813,54 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
     gA[d] = P::add(ncmR[d], cpL[d]);
     gB[d] = P::sub(cpL[d], ncmR[d]);
   }
+  // Flat space without the optical-depth weighting, with the bins numbered
+  // in sign pairs (a.sign_pairs; the fixed-row variants are launched only
+  // then): along x1 and x2 both faces of a bin take their upwind states from
+  // the same side, and both bins of a thread's pair from the same side too.
+  // Mirrored so that the upwind neighbour u1 (and u2 beyond it) lies on the
+  // left and the downwind neighbour d1 on the right,
+  //   div = X (c + q(u1, c, d1)) + Y (u1 + q(u2, u1, c)),
+  // X = cp, Y = -cm (upwind on the lower side) or X = -cm, Y = cp (upper),
+  // with q the van Leer half-slope, odd under the mirror (so the mirrored
+  // slopes carry their signs): two slopes and two coefficients per
+  // dimension instead of three and four.  mo[d] holds the element offsets
+  // of the rows u2, u1, d1 in a ring stage.
+  constexpr bool MIR = !ANG && !TAU && RC != RAD_RECON_PPM;
+  const bool mir = MIR && (NAP != 0 || a.sign_pairs);
+  V mX[2], mY[2];
+  int mo[2][3];
+  if (MIR) {
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      // the side of the element with the larger coefficient; a direction
+      // component that is zero up to rounding (a few 1e-17: lattice points on
+      // a coordinate plane) may carry either sign, and its flux is negligible
+      // whichever side it takes
+      const R ax = fabs(cm[d].x) + fabs(cp[d].x), ay = fabs(cm[d].y) + fabs(cp[d].y);
+      const bool rx = um[d] & 1, ry = um[d] & 2;
+      const bool dn = ax >= ay ? rx : ry;                // upwind on the upper side
+      if (mir && rx != ry && fmin(ax, ay) > R(1e-6) * fmax(ax, ay)) atomicOr(a.err, kErrState);
+      const V ncm = P::mk(-cm[d].x, -cm[d].y);
+      mX[d] = dn ? ncm : cp[d];
+      mY[d] = dn ? cp[d] : ncm;
+      // x1: the block rows i-2 .. i+2 in slots 0 .. 4; x2: rows j-2, j-1,
+      // j+1, j+2 in slots SX2 .. SX2 + 3
+      const int s2 = d == 0 ? (dn ? 4 : 0) : SX2 + (dn ? 3 : 0);
+      const int s1 = d == 0 ? (dn ? 3 : 1) : SX2 + (dn ? 2 : 1);
+      const int sd = d == 0 ? (dn ? 1 : 3) : SX2 + (dn ? 1 : 2);
+      const int bo = inpair ? b0 : 0;
+      mo[d][0] = s2 * nap + bo;
+      mo[d][1] = s1 * nap + bo;
+      mo[d][2] = sd * nap + bo;
+    }
+  }
+  auto divm = [&](int d, const R *sr, V c) -> V {
+    const V u1 = *(const V *)(sr + mo[d][1]);
+    if (!plm) return P::fma(mX[d], c, P::mul(mY[d], u1));
+    const V u2 = *(const V *)(sr + mo[d][0]), d1 = *(const V *)(sr + mo[d][2]);
+    const V qf = vl2<R>(u2, u1, c), qc = vl2<R>(u1, c, d1);
+    return P::fma(mX[d], P::add(c, qc), P::mul(mY[d], P::add(u1, qf)));
+  };
   auto divd = [&](int d, V m1, V c, V p1, V qm, V qc, V qp, V dl, V dh) -> V {
     if (tau) return face_div_tau<R>(um[d], up[d], cm[d], cp[d], m1, c, p1, qm, qc, qp, dl, dh);
     if (ANG) return face_div<R>(um[d], up[d], cm[d], cp[d], m1, c, p1, qm, qc, qp);
@@ -1091,6 +1140,8 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       V loL, loR, hiL, hiR;
       ppm_states<R>(v, loL, loR, hiL, hiR);
       sx = P::add(sx, divs(0, loL, loR, hiL, hiR, dlo[0], dhi[0]));
+    } else if (mir) {
+      sx = P::add(sx, divm(0, sr, zc));
     } else {
       const V m2 = sv(sr), m1 = sv(sr + nap), q1 = sv(sr + 3 * nap), q2 = sv(sr + 4 * nap);
       V sm = zero, sc = zero, sp = zero;
@@ -1112,6 +1163,8 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       V loL, loR, hiL, hiR;
       ppm_states<R>(v, loL, loR, hiL, hiR);
       sx = P::add(sx, divs(1, loL, loR, hiL, hiR, dlo[1], dhi[1]));
+    } else if (a.ndim >= 2 && mir) {
+      sx = P::add(sx, divm(1, sr, zc));
     } else if (a.ndim >= 2) {
       V yv[4];
 #pragma unroll

@@ -35,6 +35,21 @@ def test_angle_grid_matches_oracle(level):
         rad.rad_destroy(ctx)
 
 
+@pytest.mark.parametrize("level", [3, 4, 5, 7, 8, 9])
+def test_bins_are_numbered_in_sign_pairs(level):
+    """The library numbers its bins so that bins 2t and 2t + 1 have no
+    direction component of opposite sign (the flat-space stage kernel's
+    threads own such pairs); these levels admit a full pairing."""
+    ctx = rad.rad_create()
+    try:
+        na, _ = rad.rad_init_angles(ctx, level)
+        d, _, _ = rad.rad_get_angles(ctx, na)
+        s = np.where(np.abs(d) < 1e-12, 0.0, np.sign(d))
+        assert (s[0::2] * s[1::2] >= 0).all()
+    finally:
+        rad.rad_destroy(ctx)
+
+
 @pytest.mark.parametrize("name,n,level", [("turb3d", (8, 6, 4), 2), ("torus3d", (8, 6, 4), 3),
                                           ("adjoint2d", (12, 8, 1), 2)])
 def test_cfl_matches_oracle(name, n, level):
