@@ -609,7 +609,9 @@ def run_e2e(args, rad, ctx, dt, opts, prec, mom, sh, na, nap, tdt, dev, world):
     return {"value": rate, "unit": "cell-angle updates/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "h2d_gbs_measured": round(h2d_gbs, 1), "h2d_gbs_before": round(gbs_before, 1),
-            "upload_bound_value": sh[0] * sh[1] * sh[2] * na / (h2d / (h2d_gbs * 1e9)),
+            # the rate the uploads alone allow at the better of the two link
+            # measurements (what the link showed it can sustain)
+            "upload_bound_value": sh[0] * sh[1] * sh[2] * na / (h2d / (max(h2d_gbs, gbs_before) * 1e9)),
             "api": "rad_step_host (host buffers; uploads, read-backs and moments on their own streams, overlapping the steps)",
             "reads_back": "the step's results: moments R^{AB} [cell][10] and gas temperature T [cell]; the evolved "
                           "intensity stays on the device (rad_host_item.I_out is null)"}
