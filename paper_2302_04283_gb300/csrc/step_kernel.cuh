@@ -774,6 +774,14 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   // primitive recovery factor (0 for guarded or inactive bins)
   const V inv_f = P::mk((act0 && !g0) ? R(1) / fconv.x : R(0), (act1 && !g1) ? R(1) / fconv.y : R(0));
   const V keep = P::mk((act0 && !g0) ? R(1) : R(0), (act1 && !g1) ? R(1) : R(0));   // 0: guarded or padding
+  // The stage combination of U = n^0 n_0 I, U* = U^{s-1} + dt L (stage 1) or
+  // (U^0 + U^1 + dt L) / 2 (stage 2) with L = -(divS + divA), taken back to
+  // I* = U* / (n^0 n_0) in one affine step (the FP64 kernels): I* = kS
+  // (I^{s-1} [+ I^0]) + kD div with kS = 1 (1/2 in stage 2) and kD = -dt /
+  // (n^0 n_0) (halved in stage 2); both 0 for guarded and padding bins.
+  const R hs = ST2 ? R(0.5) : R(1);
+  const V kS = P::mul(P::mk(hs, hs), keep);
+  const V kD = P::mul(P::mk(-hs * (R)a.dt, -hs * (R)a.dt), inv_f);
   const R invdV = cg.invdV;
   auto fcoef = [&](const Face &F, unsigned &upR) -> V {
     V na = P::fma(nhz, P::mk(F.ea[3], F.ea[3]),
@@ -827,11 +835,16 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
   // of the rows u2, u1, d1 in a ring stage.
   constexpr bool MIR = !ANG && !TAU && RC != RAD_RECON_PPM;
   const bool mir = MIR && (NAP != 0 || a.sign_pairs);
-  V mX[2], mY[2];
+  // In FP64 x3 takes the same form from the register window (its selects run
+  // on the integer pipe, beside the FP64 pipe that bounds that kernel); mXs
+  // is X with the sign of the mirror, which multiplies the own slope.
+  constexpr bool MIR3 = MIR && sizeof(R) == 8;
+  V mX[3], mY[3], mXs = P::mk(R(0), R(0));
+  bool dn3 = false;
   int mo[2][3];
   if (MIR) {
 #pragma unroll
-    for (int d = 0; d < 2; ++d) {
+    for (int d = 0; d < (MIR3 ? 3 : 2); ++d) {
       // the side of the element with the larger coefficient; a direction
       // component that is zero up to rounding (a few 1e-17: lattice points on
       // a coordinate plane) may carry either sign, and its flux is negligible
@@ -843,6 +856,11 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       const V ncm = P::mk(-cm[d].x, -cm[d].y);
       mX[d] = dn ? ncm : cp[d];
       mY[d] = dn ? cp[d] : ncm;
+      if (d == 2) {
+        dn3 = dn;
+        mXs = dn ? P::mk(-mX[2].x, -mX[2].y) : mX[2];
+        continue;
+      }
       // x1: the block rows i-2 .. i+2 in slots 0 .. 4; x2: rows j-2, j-1,
       // j+1, j+2 in slots SX2 .. SX2 + 3
       const int s2 = d == 0 ? (dn ? 4 : 0) : SX2 + (dn ? 3 : 0);
@@ -1123,7 +1141,15 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       const V qc = plm ? vl2<R>(w2, w3, w4) : zero;   // slope of k+1
       zc = w2;
       // slopes: qa = slope(k-1), qb = slope(k), qc = slope(k+1)
-      sx = divd(2, w1, w2, w3, qa, qb, qc, dlo[2], dhi[2]);
+      if (MIR3 && mir) {
+        // upwind frame: u1 = w1 or w3, its mirrored slope qa or -qc, the
+        // own mirrored slope +-qb (the sign in mXs)
+        const V u1 = dn3 ? w3 : w1;
+        sx = plm ? P::fma(mX[2], w2, P::fma(mXs, qb, P::mul(mY[2], P::add(u1, dn3 ? P::mk(-qc.x, -qc.y) : qa))))
+                 : P::fma(mX[2], w2, P::mul(mY[2], u1));
+      } else {
+        sx = divd(2, w1, w2, w3, qa, qb, qc, dlo[2], dhi[2]);
+      }
       w0 = w1;
       w1 = w2;
       w2 = w3;
@@ -1266,10 +1292,18 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
     // U* = U^{s-1} + dt L   (stage 1)   or   U^0/2 + (U^1 + dt L)/2   (stage 2), L = -(divS + divA)
     if (ANG) sx = P::add(sx, divA);
     if (EXT && a.divF) sx = P::add(sx, __ldg((const V *)((const R *)a.divF + (unsigned)(k0 + c) * strideK + own)));
-    V Us = P::fma(P::mk(-dtR, -dtR), sx, P::mul(fconv, zc));   // L = -(divS + divA)
-    if (ST2) {
-      const V U0 = P::mul(fconv, sv(sr + SI0 * nap));
-      Us = P::mul(P::mk(R(0.5), R(0.5)), P::add(U0, Us));
+    // FP64: the affine form (fewer FP64-pipe operations); FP32: U* first and
+    // I* after the release (the FP32 kernels' register allocation prefers it)
+    constexpr bool AFF = sizeof(R) == 8;
+    V Is = zero, Us = zero;
+    if (AFF) {
+      Is = ST2 ? P::fma(kS, P::add(sv(sr + SI0 * nap), zc), P::mul(kD, sx)) : P::fma(kS, zc, P::mul(kD, sx));
+    } else {
+      Us = P::fma(P::mk(-dtR, -dtR), sx, P::mul(fconv, zc));   // L = -(divS + divA)
+      if (ST2) {
+        const V U0 = P::mul(fconv, sv(sr + SI0 * nap));
+        Us = P::mul(P::mk(R(0.5), R(0.5)), P::add(U0, Us));
+      }
     }
     // every read of this ring stage is done: release it to the producer now,
     // so that the next copies overlap this cell's coupling sums (the
@@ -1279,7 +1313,7 @@ __global__ void __launch_bounds__((sizeof(R) == 4 && !ANG && RC != RAD_RECON_PPM
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&ebars[st])) : "memory");
     }
-    const V Is = P::mul(Us, inv_f);
+    if (!AFF) Is = P::mul(Us, inv_f);
     if (inpair) *(V *)(sI + c * nap + b0) = Is;
     if (a.Istar && inpair) *(V *)((R *)a.Istar + (unsigned)(k0 + c) * strideK + own) = Is;
     if (couple) {
