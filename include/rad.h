@@ -417,7 +417,11 @@ int rad_step_adjoint(rad_ctx *ctx, const void *I_n, const rad_gas *gas, double d
 int rad_loss_outer(rad_ctx *ctx, const void *I, int precision, double *L_dev, void *dL_dI);
 
 /* Read and clear the sticky device error word.  Synchronous.  Returns
- * RAD_OK or the first recorded rad_status. */
+ * RAD_OK or one recorded status, in this order: RAD_ECUDA (a bounded device
+ * wait gave up), RAD_ENOCONV (a quartic without a bracketed root, or a gas
+ * update that did not converge), RAD_ENONFINITE (a non-finite intensity),
+ * RAD_ESTATE (a flat-space stage met a bin pair with opposite upwind sides,
+ * which the library's bin numbering excludes). */
 int rad_check(rad_ctx *ctx);
 
 /* Self-test of the bounded device waits (no paper counterpart): enqueue a
