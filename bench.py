@@ -37,10 +37,15 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "turb3d"
 # FP64 arithmetic of one cell-angle update (both RK stages) of the flat PLM
-# thermal step, counted from the stage kernel: 7 limiter slopes, 3 weighted
-# face pairs, the stage combination, the coupling sums and update and the
-# gas-source terms, ~119 flops per stage
-FLOPS_PER_UPDATE = 238
+# thermal step, counted from the stage kernel (an FMA as 2, a division as 1),
+# per stage: x1 and x2 in the upwind frame, 14 each (three differences, two
+# van Leer slopes, the two upwind face states and their weights); x3 from the
+# register window, 11 (one new slope, the face pair); the stage combination
+# and the sum of the three divergences, 5.5; the coupling sums, 20 (n0bar,
+# the weights and the per-bin and warp sums); the implicit update and guard,
+# 19; the gas-source terms, 8; ~92 per stage, with the per-cell quartic and
+# gas source adding ~1 per update
+FLOPS_PER_UPDATE = 184
 FP64_PEAK_TFLOPS = 1.25
 WORKLOAD_TEXT = ("turb3d: flat-space Cartesian 128^3, geodesic level 4 (162 bins), periodic, moving gas "
                  "|v|<=0.5, log-uniform opacities, PLM, thermal coupling")
