@@ -61,6 +61,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--n", type=int, default=None, help="cells per side (default: the workload's 128)")
+    p.add_argument("--workload", default=WORKLOAD, choices=["turb3d", "torus3d", "torus3d_big"],
+                   help="the stepped workload: turb3d (the benchmark); the Kerr-Schild ones time and "
+                        "profile the curved-space kernels and run only with --no-e2e --no-extras "
+                        "--no-cpu-baseline")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the FP64-path, accuracy and adjoint/forward measurements")
     p.add_argument("--replicas", action="store_true", help="N > 1: unconnected replicas instead of blocks")
@@ -162,7 +166,10 @@ def setup_gpu(prec, dev, n=None, name=WORKLOAD, block=None):
     import torch
     import paper_2302_04283_gb300 as rad
     import workloads as W
-    w = W.make(name, n=(n, n, n) if n else None, with_intensity=False)
+    # --n scales the workload's grid: n^3 for the Cartesian box, n x n/2 x n/2
+    # (the default aspect) for the Kerr-Schild ones
+    shape = None if not n else ((n, n, n) if name == WORKLOAD else (n, n // 2, n // 2))
+    w = W.make(name, n=shape, with_intensity=False)
     ctx = rad.rad_create(torch.cuda.current_stream())
     na, nap = rad.rad_init_angles(ctx, w["level"])
     xf, bc = w["xf"], w["bc"]
@@ -246,7 +253,7 @@ def run_ours(args, rank, world):
     dev = f"cuda:{int(os.environ.get('LOCAL_RANK', 0))}"
     torch.cuda.set_device(dev)
     blocks = (world > 1 and not args.replicas) or (world == 1 and args.decomp_self)
-    rad, w, ctx, na, nap, dt, sh, tdt, I, gas = setup_gpu(args.precision, dev, args.n,
+    rad, w, ctx, na, nap, dt, sh, tdt, I, gas = setup_gpu(args.precision, dev, args.n, name=args.workload,
                                                           block=(rank, world) if blocks else None)
     if blocks and world > 1:
         dt_t = torch.tensor([dt], dtype=torch.float64, device=dev)
@@ -313,7 +320,7 @@ def run_ours(args, rank, world):
     achieved = bytes_step * args.steps / (stage_ms * 1e-3) / 1e9
     pk = peaks()
     hbm = pk.get("hbm_gbs")
-    traffic = profiled_traffic(args.precision, ncell)
+    traffic = profiled_traffic(args.precision, ncell) if args.workload == WORKLOAD else None
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm or 6800.0,
             "unit": "GB/s", "frac": round(achieved / (hbm or 6800.0), 4),
             "traffic": None if traffic is None else round(traffic),
@@ -336,8 +343,11 @@ def run_ours(args, rank, world):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.precision == "f32" else "f64",
-        "data": "synthetic (seeded turbulent-gas workload; no dataset in the paper)",
-        "config": {"workload": WORKLOAD_TEXT,
+        "data": ("synthetic (seeded turbulent-gas workload; no dataset in the paper)" if args.workload == WORKLOAD
+                 else "synthetic (seeded torus-gas workload; no dataset in the paper)"),
+        "config": {"workload": WORKLOAD_TEXT if args.workload == WORKLOAD else
+                   f"{args.workload}: Kerr-Schild a={w['spin']}, {w['n'][0]}x{w['n'][1]}x{w['n'][2]} cells, "
+                   f"geodesic level {w['level']} ({na} bins)",
                    "cells": ncell, "bins": na, "precision": args.precision,
                    "moments": "split-bf16 tensor cores" if mom == rad.RAD_MOM_BF16X3 else "CUDA cores",
                    "l2": "inputs larger than L2 (I is %.2f GB), no flush" % (ncell * nap * esz / 1e9),
@@ -742,7 +752,9 @@ def run_reference(args):
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded turbulent-gas workload; no dataset in the paper)",
-            "config": {"workload": WORKLOAD_TEXT, "cells": 128 ** 3, "bins": 162,
+            "config": {"workload": WORKLOAD_TEXT if args.workload == WORKLOAD else
+                   f"{args.workload}: Kerr-Schild a={w['spin']}, {w['n'][0]}x{w['n'][1]}x{w['n'][2]} cells, "
+                   f"geodesic level {w['level']} ({na} bins)", "cells": 128 ** 3, "bins": 162,
                        "sample": f"each step advances a {o.n[0]}^3-cell block of the same recipe (bounded CPU "
                                  "work); the rate is per cell-angle update, comparable with the GPU arm"},
             "cpu_baseline": info, "e2e": {"value": v, "unit": "cell-angle updates/s",
@@ -751,6 +763,8 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.workload != WORKLOAD and not (args.no_e2e and args.no_extras and args.no_cpu_baseline):
+        raise SystemExit("--workload other than turb3d runs only with --no-e2e --no-extras --no-cpu-baseline")
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":
