@@ -59,3 +59,13 @@ def test_reference_arm_prints_once_under_torchrun():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_other_workloads_run_only_without_the_headline_legs():
+    """bench.py --workload torus3d is a profiling run of the curved-space
+    kernels: without --no-e2e --no-extras --no-cpu-baseline it is refused
+    before any device work, so the benchmark line is always turb3d's."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--workload", "torus3d"],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0
+    assert "--no-e2e --no-extras --no-cpu-baseline" in (r.stdout + r.stderr)
