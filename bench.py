@@ -256,9 +256,8 @@ def run_ours(args, rank, world):
     rad, w, ctx, na, nap, dt, sh, tdt, I, gas = setup_gpu(args.precision, dev, args.n, name=args.workload,
                                                           block=(rank, world) if blocks else None)
     if blocks and world > 1:
-        dt_t = torch.tensor([dt], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(dt_t, op=torch.distributed.ReduceOp.MIN)     # the domain's bound
-        dt = float(dt_t.item())
+        from paper_2302_04283_gb300 import blocks as B
+        dt = B.domain_dt(dt, device=dev)                                        # the domain's bound
     ncell = sh[0] * sh[1] * sh[2]
     esz = 4 if args.precision == "f32" else 8
     prec = rad.RAD_F32 if args.precision == "f32" else rad.RAD_F64

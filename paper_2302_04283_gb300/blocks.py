@@ -12,7 +12,9 @@ parts[2] blocks (rank r is block (p1, p2, p3) with r = (p3 P2 + p2) P1 + p1)
 and gives each block's cells, face coordinates, boundary kinds and
 neighbours.  `exchange` moves the halo buffers between ranks with
 torch.distributed point-to-point messages (NCCL for device tensors, gloo for
-host tensors); `step_block` is one RK2 step of a block through the C ABI.
+host tensors); `step_block` is one RK2 step of a block through the C ABI;
+`domain_dt` and `domain_loss` reduce the blocks' time-step bounds (minimum)
+and outgoing-flux losses (sum) over the ranks.
 Nothing here does arithmetic of the method."""
 import torch
 import torch.distributed as dist
@@ -99,6 +101,28 @@ def exchange(neighbours, send, recv, group=None):
     if ops:
         for req in dist.batch_isend_irecv(ops):
             req.wait()
+
+
+def domain_dt(dt, group=None, device=None):
+    """The whole domain's time step: the smallest of the blocks' CFL bounds
+    (one all-reduce; every rank gets it)."""
+    t = torch.tensor([float(dt)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MIN, group=group)
+    return float(t.item())
+
+
+def owns_outer_x1(dec, rank):
+    """Whether the block holds the domain's last x1 cells, where the
+    outgoing-flux loss is taken (rad_loss_outer on that block)."""
+    return dec.coords(rank)[0] == dec.parts[0] - 1
+
+
+def domain_loss(L, group=None):
+    """The whole domain's outgoing-flux loss from each block's part (0 from a
+    block that does not own the outer x1 face): an all-reduce sum, in place
+    on the one-element tensor L, which is returned."""
+    dist.all_reduce(L, op=dist.ReduceOp.SUM, group=group)
+    return L
 
 
 def halo_buffers(ctx_shape, neighbours, nap, dtype, device):

@@ -2,7 +2,11 @@
 advance one block of the domain with the oracle, exchanging the ghost layers
 of their shared faces before every stage through
 paper_2302_04283_gb300.blocks.exchange (the same routine the GPU blocks use),
-and their blocks must equal the undivided oracle run bit for bit.  Covers a
+and their blocks must equal the undivided oracle run bit for bit; the
+domain's time step (blocks.domain_dt, the minimum of the blocks' bounds)
+must equal the undivided bound, and its outgoing-flux loss
+(blocks.domain_loss over the blocks that own the outer x1 cells) the
+undivided loss to rounding.  Covers a
 periodic direction split in two (both faces of each block shared with the
 same neighbour) and a Kerr-Schild grid split across theta (each block keeps
 a polar axis and shares one face)."""
@@ -76,7 +80,14 @@ def _worker(rank, world, port, case, q):
             assert bool(ok.all())
         same = (torch.equal(I, If[cut]), torch.equal(T, Tf[cut]), torch.equal(src, srcf[cut]))
         dif = float((I - If[cut]).abs().max() / If[cut].abs().max())
-        q.put((rank, same, dif, len(nb)))
+        # the domain's time step from the blocks' bounds, and its
+        # outgoing-flux loss from the blocks' parts
+        dt_dom = B.domain_dt(OCFL.cfl_dt(st, w["cfl"]))
+        from oracle import adjoint as OA
+        Lb = OA.loss_outer(I, st) if B.owns_outer_x1(dec, rank) else torch.zeros((), dtype=I.dtype)
+        L = float(B.domain_loss(Lb.reshape(1).clone())[0])
+        Lf = float(OA.loss_outer(If, full))
+        q.put((rank, same, dif, len(nb), abs(dt_dom - dt) / dt, abs(L - Lf) / abs(Lf)))
     finally:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -94,9 +105,11 @@ def test_split_domain_equals_undivided_oracle(case):
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
-    for rank, same, dif, nnb in out:
+    for rank, same, dif, nnb, ddt, dL in out:
         assert nnb >= 1
         assert all(same), (case, rank, same, dif)
+        assert ddt == 0.0, ddt              # a minimum of the same per-cell bounds
+        assert dL < 1e-13, dL               # the same terms summed in another order
 
 
 def test_decomposition_faces_and_neighbours():
