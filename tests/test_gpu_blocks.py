@@ -4,7 +4,8 @@ stage at a time with rad_step_stage after its neighbours' rad_halo_pack
 layers have been copied into its halo buffers (the exchange that messages
 between GPUs perform in a multi-GPU run).  The assembled result must equal
 rad_step on the undivided domain bit for bit: the per-cell arithmetic does
-not depend on the block.  Also: the calls that refuse shared faces."""
+not depend on the block; the blocks' outgoing-flux losses add up to the
+undivided loss.  Also: the calls that refuse shared faces."""
 import numpy as np
 import pytest
 import torch
@@ -97,6 +98,17 @@ def test_blocks_equal_the_undivided_step(name, n, level, parts, prec, recon, rec
         assert torch.equal(b["I"], I[b["sl"]])
         assert torch.equal(b["gas"]["T"], g["T"][b["sl"]])
         assert torch.equal(b["src"], src[b["sl"]])
+    # the domain's outgoing-flux loss: the parts of the blocks that hold the
+    # outer x1 cells (their sum is what blocks.domain_loss all-reduces)
+    L = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rad.rad_loss_outer(ctx, I, o.precision, L)
+    parts_L = []
+    for r, b in enumerate(blocks):
+        if B.owns_outer_x1(dec, r):
+            Lb = torch.zeros(1, dtype=torch.float64, device="cuda")
+            rad.rad_loss_outer(b["ctx"], b["I"], o.precision, Lb)
+            parts_L.append(float(Lb))
+    assert abs(sum(parts_L) - float(L)) <= 1e-13 * abs(float(L))
     for b in blocks:
         rad.rad_destroy(b["ctx"])
     rad.rad_destroy(ctx)
